@@ -1,0 +1,84 @@
+"""Statistical pins of the whole oracle chain (RNG keying, bond rule, labelling,
+recolouring together) against exact results it does not compute:
+brute-force enumeration, transfer matrices and Baxter's closed form for the
+critical energy, u(T_c) = -(1 + 1/sqrt q)."""
+import numpy as np
+import pytest
+
+import oracle
+from tests import exact
+
+
+def _batch_mean(x, nb=50):
+    x = np.asarray(x, dtype=np.float64)
+    m = len(x) // nb
+    b = x[: m * nb].reshape(nb, m).mean(1)
+    return b.mean(), b.std(ddof=1) / np.sqrt(nb)
+
+
+def _chain(L, q, T, seed, n, burn=200):
+    _, E, nn = oracle.run(L, q, T, seed, n + burn)
+    return E[burn:].astype(np.float64), nn[burn:].astype(np.float64)
+
+
+@pytest.mark.parametrize("q", [2, 3, 4, 5])
+def test_3x3_moments_match_enumeration(q):
+    T = oracle.tc(q)
+    E, n = _chain(3, q, T, seed=1000 + q, n=200_000)
+    e1, e2, nm = exact.brute_moments(3, q, T)
+    for data, ref in [(E, e1), (E * E, e2), (n.max(1), nm)]:
+        m, s = _batch_mean(data)
+        assert abs(m - ref) < 5 * s + 1e-9, (m, ref, s)
+
+
+@pytest.mark.parametrize("q,T", [(2, 1.0), (2, 2.0), (3, 0.9)])
+def test_3x3_off_critical(q, T):
+    E, _ = _chain(3, q, T, seed=77, n=100_000)
+    e1, _, _ = exact.brute_moments(3, q, T)
+    m, s = _batch_mean(E)
+    assert abs(m - e1) < 5 * s
+
+
+def test_4x4_ising_moments_match_enumeration():
+    q, T = 2, oracle.tc(2)
+    E, n = _chain(4, q, T, seed=4242, n=150_000)
+    e1, e2, nm = exact.brute_moments(4, q, T)
+    for data, ref in [(E, e1), (E * E, e2), (n.max(1), nm)]:
+        m, s = _batch_mean(data)
+        assert abs(m - ref) < 5 * s
+
+
+@pytest.mark.parametrize("L,q", [(8, 2), (5, 3), (4, 4)])
+def test_torus_energy_matches_transfer_matrix(L, q):
+    T = oracle.tc(q)
+    e1, e2 = exact.transfer_moments(L, L, q, T)
+    # cross-check the transfer matrix itself against enumeration where possible
+    if q ** (L * L) <= 2 ** 16:
+        b1, b2, _ = exact.brute_moments(L, q, T)
+        assert abs(e1 - b1) < 1e-6 * b1 and abs(e2 - b2) < 1e-6 * b2
+    E, _ = _chain(L, q, T, seed=31 * L + q, n=60_000)
+    for data, ref in [(E, e1), (E * E, e2)]:
+        m, s = _batch_mean(data)
+        assert abs(m - ref) < 5 * s, (m, ref, s)
+
+
+def test_chain_statistics_catch_a_wrong_probability():
+    """Run the same chain at a temperature 5% off (what a mistake in p would
+    do): the 3x3 check must reject it."""
+    q, T = 2, oracle.tc(2)
+    E, _ = _chain(3, q, T * 1.05, seed=5, n=100_000)
+    e1, _, _ = exact.brute_moments(3, q, T)
+    m, s = _batch_mean(E)
+    assert abs(m - e1) > 5 * s
+
+
+@pytest.mark.parametrize("q", [2, 3])
+def test_critical_energy_baxter(q):
+    """-E_sat/N at T_c approaches -(1+1/sqrt q) (Baxter); at L=128 the
+    finite-size shift is well below the 0.01 tolerance used here."""
+    L = 128
+    T = oracle.tc(q)
+    E, _ = _chain(L, q, T, seed=900 + q, n=400, burn=100)
+    u = -E / (L * L)
+    m, s = _batch_mean(u, nb=20)
+    assert abs(m + (1 + 1 / np.sqrt(q))) < 5 * s + 0.01
