@@ -1,0 +1,192 @@
+/*
+ * sw.h -- C ABI of the GB300 Swendsen-Wang library (libswgb.so).
+ *
+ * One Swendsen-Wang (SW) multi-cluster sweep of the periodic 2D q-state
+ * Potts model H = -J sum_<ij> delta(s_i, s_j), J = 1 (Komura & Okabe,
+ * Sec. 2, Eq. 1 up to the constant -J per bond), on one GPU:
+ *   (1) bond activation between equal nearest-neighbour spins with
+ *       probability p = 1 - exp(-1/T)                       (Sec. 2, step 1)
+ *   (2) connected-component labelling of the bond graph; a cluster's label
+ *       is its smallest site index, the Hoshen-Kopelman "proper label"
+ *                                                          (Sec. 2, step 2)
+ *   (3) a uniformly random new state per cluster           (Sec. 2, step 3)
+ *   (4) integer energy / magnetisation reductions ("update + measurement",
+ *       Sec. 4, Table 1).
+ *
+ * Conventions (shared with the CPU oracle so every configuration is
+ * reproduced bit for bit):
+ *   - spins are uint8 in 0..q-1, row-major, site i = y*L + x, L*L bytes;
+ *   - each site owns its right (+x) and down (+y) bond (periodic), so there
+ *     are 2N bonds; the packed bond lattice stores 2 bits per site
+ *     (bit 0 right, bit 1 down), 4 sites per byte, rows padded to
+ *     ceil(L/4) bytes: byte [y*ceil(L/4) + x/4], bits 2*(x%4)..;
+ *   - thr = floor(p * 2^32) clamped to 2^32-1; a bond is active iff the two
+ *     spins are equal and u < thr for its Philox word u;
+ *   - Philox4x32-10 (Salmon et al., SC'11), key = (seed_lo, seed_hi),
+ *     counters (lo, hi, sweep, domain): bonds (i>>1, sweep, 0) word
+ *     2*(i&1)+dir; new state of the cluster with root r (r, sweep, 1) word 0;
+ *     initial spins (i>>2, 0, 2) word i&3; a word w picks floor(w*q/2^32);
+ *   - E_sat = satisfied bonds (0..2N); the paper's energy is -E_sat (Eq. 1
+ *     without the constant) and 2N - E_sat with it; n[s] = sites in state s.
+ *
+ * Errors: every call returns SW_OK (0) or a negative SW_ERR_* code.  Errors
+ * on a handle are sticky: once a call fails with SW_ERR_CUDA / SW_ERR_DEVICE
+ * the handle refuses further work; sw_strerror() names every code.
+ * Ownership: the library owns all device memory of a handle (allocated at
+ * create through the allocator installed with sw_set_allocator, cudaMalloc
+ * by default) and frees it in sw_destroy.  Host buffers passed in are owned
+ * by the caller and only read/written during the call.  Device buffers
+ * passed in must stay valid until the work enqueued on the handle's stream
+ * has completed.  A handle is not thread-safe; distinct handles are.
+ * All work is enqueued on the handle's stream (sw_bind_stream; default: the
+ * legacy default stream); calls that return host data synchronise it.
+ */
+#ifndef SWGB_SW_H
+#define SWGB_SW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SW_OK 0
+#define SW_ERR_INVAL (-1)   /* bad argument (L < 2, q not in [2,255], T <= 0 or
+                               not finite, null pointer, size mismatch, ...) */
+#define SW_ERR_NOMEM (-2)   /* device or host allocation failed */
+#define SW_ERR_CUDA (-3)    /* a CUDA runtime call failed */
+#define SW_ERR_TIMEOUT (-4) /* a bounded device loop hit its iteration cap */
+#define SW_ERR_STATE (-5)   /* call not valid in the handle's state */
+#define SW_ERR_DEVICE (-6)  /* a device-side consistency check failed */
+#define SW_ERR_RANGE (-7)   /* requested observables are not (or no longer)
+                               held in the observable ring */
+
+#define SW_INIT_RANDOM 0u   /* spins from the init stream (default) */
+#define SW_INIT_ZERO 1u     /* all spins in state 0 */
+
+typedef struct sw_sim sw_sim;
+
+/* Observables of one configuration (Sec. 4: energy and magnetisation). */
+typedef struct {
+  uint64_t config; /* configuration index = sweeps applied since create */
+  uint64_t E_sat;  /* satisfied bonds, 0..2N */
+  uint32_t q;      /* number of states; n[0..q-1] are valid */
+  uint32_t pad_;
+  uint64_t n[256]; /* sites in each state */
+} sw_obs;
+
+/* Creation parameters; zero means "default" for every optional field. */
+typedef struct {
+  uint64_t L;           /* linear size, >= 2 (N = L*L sites) */
+  uint32_t q;           /* states, 2..255 */
+  uint32_t label_bits;  /* 0 = auto (32 if L <= 32768, else 64), 32 or 64:
+                           width of the global cluster labels (site indices) */
+  double T;             /* temperature in units of J, finite, > 0 */
+  uint64_t seed;        /* Philox key */
+  uint32_t tile_h;      /* labelling tile height: 0 = auto, or 16/32/64/128
+                           (tile width is 128 sites); results do not depend
+                           on it */
+  uint32_t ring;        /* observable ring capacity in configurations,
+                           0 = 1024 */
+  uint32_t init;        /* SW_INIT_RANDOM or SW_INIT_ZERO */
+  uint32_t store_bonds; /* 1 = keep the packed bond lattice of the latest
+                           sweep (sw_bonds); costs 0.25 B/site per sweep */
+  uint32_t measure;     /* 0 = default (on); 2 = off: sweeps record no
+                           observables ("update only", Sec. 4 Table 1) */
+  uint32_t reserved[3];
+} sw_params;
+
+/* Library-wide device allocator (e.g. a framework's caching allocator).
+ * alloc returns a device pointer of at least `bytes` bytes (256-byte
+ * aligned) or NULL; free releases it.  Applies to handles created after the
+ * call.  Passing NULL for both restores cudaMalloc/cudaFree. */
+typedef void *(*sw_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*sw_free_fn)(void *ptr, size_t bytes, void *ctx);
+int sw_set_allocator(sw_alloc_fn alloc, sw_free_fn free_fn, void *ctx);
+
+/* Create a simulation of the L x L lattice at temperature T with Philox key
+ * `seed`; spins start from the init stream, the sweep counter at 0.
+ * (The problem statement of Sec. 2: L, q, T, periodic boundaries.) */
+int sw_create(uint64_t L, uint32_t q, double T, uint64_t seed, sw_sim **out);
+/* Same with every option of sw_params. */
+int sw_create_ex(const sw_params *params, sw_sim **out);
+/* Free the handle and all its device memory (synchronises its stream). */
+void sw_destroy(sw_sim *sim);
+
+/* Enqueue later work on `stream` (a cudaStream_t; NULL = default stream). */
+int sw_bind_stream(sw_sim *sim, void *stream);
+
+/* Run n full SW sweeps (steps 1-3 of Sec. 2 plus the fused measurement of
+ * each configuration the sweeps read).  Asynchronous on the handle's
+ * stream. */
+int sw_sweep(sw_sim *sim, uint64_t n);
+
+/* Observables of the current configuration (synchronises). */
+int sw_measure(sw_sim *sim, sw_obs *out);
+
+/* Observables of configurations first .. first+count-1 (configuration c =
+ * the state after c sweeps).  E receives count values, n receives count*q
+ * values (row-major); either may be NULL.  Fails with SW_ERR_RANGE if a
+ * configuration was not measured (created before the last sw_set_spins /
+ * sw_set_sweep, swept with measurement off) or has left the ring.
+ * Synchronises. */
+int sw_series(sw_sim *sim, uint64_t first, uint64_t count, uint64_t *E,
+              uint64_t *n);
+
+/* Copy the L*L spins out to dst (host, or device if dst_on_device).
+ * n must equal L*L.  Synchronises for a host destination. */
+int sw_spins(sw_sim *sim, uint8_t *dst, uint64_t n, int dst_on_device);
+/* Replace the configuration (values must be < q; checked on the host for
+ * host sources).  The sweep counter is unchanged. */
+int sw_set_spins(sw_sim *sim, const uint8_t *src, uint64_t n,
+                 int src_on_device);
+
+/* Packed bond lattice of the most recent sweep (layout above); nbytes must
+ * equal L*ceil(L/4).  Requires store_bonds = 1. */
+int sw_bonds(sw_sim *sim, uint8_t *dst, uint64_t nbytes, int dst_on_device);
+
+/* Sweep counter (the Philox "sweep" counter word of the next sweep); with
+ * the spins it is the whole state of a run, so get + spins, then set +
+ * set_spins, resumes a run bit for bit. */
+int sw_get_sweep(const sw_sim *sim, uint64_t *sweep);
+int sw_set_sweep(sw_sim *sim, uint64_t sweep);
+
+/* Block until the handle's queued work is done; reports device-side errors
+ * (SW_ERR_TIMEOUT / SW_ERR_DEVICE) raised by that work. */
+int sw_sync(sw_sim *sim);
+
+/* Static facts about a handle. */
+typedef struct {
+  uint64_t L;
+  uint32_t q;
+  uint32_t thr;          /* integer bond threshold in use */
+  uint32_t label_bits;   /* 32 or 64 */
+  uint32_t tile_w, tile_h;
+  uint32_t ring;
+  uint64_t device_bytes; /* device memory held by the handle */
+  uint64_t tiles;
+} sw_info_t;
+int sw_info(const sw_sim *sim, sw_info_t *out);
+
+/* Integer bond threshold floor((1 - exp(-1/T)) * 2^32), clamped. */
+int sw_threshold(double T, uint32_t *thr);
+
+/* Step (2) alone, for a given bond lattice: label the packed bond lattice
+ * `bonds` (device, layout above, L*ceil(L/4) bytes) and write, per site, the
+ * smallest site index of its cluster to `roots` (device, L*L entries of
+ * uint32 if label_bits == 32 (requires L*L <= 2^32), else uint64).
+ * tile_h as in sw_params.  Scratch memory is taken from the allocator and
+ * released before return; runs on `stream` and synchronises it. */
+int sw_label_bonds(uint64_t L, const uint8_t *bonds, void *roots,
+                   uint32_t label_bits, uint32_t tile_h, void *stream);
+
+/* Name of an error code. */
+const char *sw_strerror(int code);
+/* Last error recorded on the handle (SW_OK if none). */
+int sw_last_error(const sw_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWGB_SW_H */

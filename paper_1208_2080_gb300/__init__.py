@@ -1,0 +1,16 @@
+"""GB300-native Swendsen-Wang sweep of the periodic 2D q-state Potts model.
+
+The computation lives in libswgb.so (CUDA, sm_103a; C ABI in include/sw.h);
+this package is its thin Python binding.  See ``Sim`` (one lattice),
+``label_bonds`` (labelling step alone) and ``threshold``.
+"""
+from ._binding import (  # noqa: F401
+    EXPORTS, LIB_PATH, Sim, SwError, check, label_bonds, lib, pack_bonds, strerror, threshold,
+    unpack_bonds, use_cuda_malloc, use_torch_allocator,
+)
+
+
+def tc(q):
+    """Critical temperature of the 2D q-state Potts model, 1/ln(1+sqrt q)."""
+    import math
+    return 1.0 / math.log1p(math.sqrt(q))

@@ -1,0 +1,303 @@
+"""ctypes binding of libswgb.so, the C ABI declared in include/sw.h.
+
+Argument marshalling only: every step of a sweep runs in the library's CUDA
+kernels.  PyTorch is used for device memory (its caching allocator is
+installed as the library's allocator) and streams.  There is no CPU
+fallback: if the library is missing or cannot be loaded, every entry point
+raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libswgb.so")
+
+SW_OK = 0
+SW_ERR_INVAL = -1
+SW_ERR_NOMEM = -2
+SW_ERR_CUDA = -3
+SW_ERR_TIMEOUT = -4
+SW_ERR_STATE = -5
+SW_ERR_DEVICE = -6
+SW_ERR_RANGE = -7
+SW_INIT_RANDOM = 0
+SW_INIT_ZERO = 1
+
+# every symbol include/sw.h declares (checked by the CPU tests)
+EXPORTS = [
+    "sw_set_allocator", "sw_create", "sw_create_ex", "sw_destroy", "sw_bind_stream", "sw_sweep",
+    "sw_measure", "sw_series", "sw_spins", "sw_set_spins", "sw_bonds", "sw_get_sweep",
+    "sw_set_sweep", "sw_sync", "sw_info", "sw_threshold", "sw_label_bonds", "sw_strerror",
+    "sw_last_error",
+]
+
+
+class SwError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+class sw_obs(ctypes.Structure):
+    _fields_ = [("config", ctypes.c_uint64), ("E_sat", ctypes.c_uint64), ("q", ctypes.c_uint32),
+                ("pad_", ctypes.c_uint32), ("n", ctypes.c_uint64 * 256)]
+
+
+class sw_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_uint64), ("q", ctypes.c_uint32), ("label_bits", ctypes.c_uint32),
+                ("T", ctypes.c_double), ("seed", ctypes.c_uint64), ("tile_h", ctypes.c_uint32),
+                ("ring", ctypes.c_uint32), ("init", ctypes.c_uint32),
+                ("store_bonds", ctypes.c_uint32), ("measure", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 3)]
+
+
+class sw_info_t(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_uint64), ("q", ctypes.c_uint32), ("thr", ctypes.c_uint32),
+                ("label_bits", ctypes.c_uint32), ("tile_w", ctypes.c_uint32),
+                ("tile_h", ctypes.c_uint32), ("ring", ctypes.c_uint32),
+                ("device_bytes", ctypes.c_uint64), ("tiles", ctypes.c_uint64)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+_lib = None
+_alloc_keep = None
+_allocator_chosen = False
+
+
+def lib():
+    """The loaded library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libswgb.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    sig = {
+        "sw_set_allocator": (i32, [ALLOC_FN, FREE_FN, vp]),
+        "sw_create": (i32, [u64, u32, ctypes.c_double, u64, ctypes.POINTER(vp)]),
+        "sw_create_ex": (i32, [ctypes.POINTER(sw_params), ctypes.POINTER(vp)]),
+        "sw_destroy": (None, [vp]),
+        "sw_bind_stream": (i32, [vp, vp]),
+        "sw_sweep": (i32, [vp, u64]),
+        "sw_measure": (i32, [vp, ctypes.POINTER(sw_obs)]),
+        "sw_series": (i32, [vp, u64, u64, u64p, u64p]),
+        "sw_spins": (i32, [vp, vp, u64, i32]),
+        "sw_set_spins": (i32, [vp, vp, u64, i32]),
+        "sw_bonds": (i32, [vp, vp, u64, i32]),
+        "sw_get_sweep": (i32, [vp, u64p]),
+        "sw_set_sweep": (i32, [vp, u64]),
+        "sw_sync": (i32, [vp]),
+        "sw_info": (i32, [vp, ctypes.POINTER(sw_info_t)]),
+        "sw_threshold": (i32, [ctypes.c_double, ctypes.POINTER(ctypes.c_uint32)]),
+        "sw_label_bonds": (i32, [u64, vp, vp, u32, u32, vp]),
+        "sw_strerror": (ctypes.c_char_p, [i32]),
+        "sw_last_error": (i32, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def strerror(code):
+    try:
+        return lib().sw_strerror(int(code)).decode()
+    except Exception:  # pragma: no cover
+        return "error"
+
+
+def check(rc, what):
+    if rc != SW_OK:
+        raise SwError(rc, what)
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching
+    allocator (affects handles created afterwards).  Done automatically by
+    the first ``Sim`` unless ``use_cuda_malloc()`` was called before."""
+    global _alloc_keep, _allocator_chosen
+    _allocator_chosen = True
+    import torch
+
+    def _alloc(nbytes, _ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes)))
+        except Exception:
+            return None
+
+    def _free(ptr, _nbytes, _ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    check(lib().sw_set_allocator(a, f, None), "sw_set_allocator")
+    _alloc_keep = (a, f)
+
+
+def use_cuda_malloc():
+    """Let the library call cudaMalloc / cudaFree itself."""
+    global _alloc_keep, _allocator_chosen
+    _allocator_chosen = True
+    check(lib().sw_set_allocator(ALLOC_FN(), FREE_FN(), None), "sw_set_allocator")
+    _alloc_keep = None
+
+
+def threshold(T):
+    out = ctypes.c_uint32()
+    check(lib().sw_threshold(float(T), ctypes.byref(out)), "sw_threshold")
+    return int(out.value)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Sim:
+    """One L x L lattice on the GPU (include/sw.h handle)."""
+
+    def __init__(self, L, q, T, seed, *, label_bits=0, tile_h=0, ring=0, init="random",
+                 store_bonds=False, measure=True, stream=None):
+        if not _allocator_chosen:
+            use_torch_allocator()
+        p = sw_params()
+        p.L, p.q, p.T, p.seed = int(L), int(q), float(T), int(seed)
+        p.label_bits, p.tile_h, p.ring = int(label_bits), int(tile_h), int(ring)
+        p.init = SW_INIT_ZERO if init == "zero" else SW_INIT_RANDOM
+        p.store_bonds = 1 if store_bonds else 0
+        p.measure = 0 if measure else 2
+        h = ctypes.c_void_p()
+        self._h = None
+        check(lib().sw_create_ex(ctypes.byref(p), ctypes.byref(h)), "sw_create_ex")
+        self._h = h
+        self.L, self.q, self.T, self.seed = int(L), int(q), float(T), int(seed)
+        self.N = self.L * self.L
+        if stream is not False:
+            self.bind_stream(stream)
+
+    def close(self):
+        if self._h is not None:
+            lib().sw_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def bind_stream(self, stream=None):
+        check(lib().sw_bind_stream(self._h, _stream_handle(stream)), "sw_bind_stream")
+
+    def sweep(self, n=1):
+        check(lib().sw_sweep(self._h, int(n)), "sw_sweep")
+
+    def sync(self):
+        check(lib().sw_sync(self._h), "sw_sync")
+
+    def measure(self):
+        o = sw_obs()
+        check(lib().sw_measure(self._h, ctypes.byref(o)), "sw_measure")
+        return int(o.E_sat), np.array(o.n[: self.q], dtype=np.uint64), int(o.config)
+
+    def series(self, first, count):
+        E = np.zeros(count, dtype=np.uint64)
+        n = np.zeros((count, self.q), dtype=np.uint64)
+        check(lib().sw_series(self._h, int(first), int(count),
+                              E.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                              n.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))), "sw_series")
+        return E, n
+
+    def spins(self, out=None):
+        """Spins as an (L, L) uint8 numpy array, or into `out` (a CUDA uint8
+        torch tensor with L*L elements, filled on the handle's stream)."""
+        if out is not None:
+            assert out.is_cuda and out.numel() == self.N and out.is_contiguous()
+            check(lib().sw_spins(self._h, ctypes.c_void_p(out.data_ptr()), self.N, 1), "sw_spins")
+            return out
+        a = np.empty(self.N, dtype=np.uint8)
+        check(lib().sw_spins(self._h, a.ctypes.data_as(ctypes.c_void_p), self.N, 0), "sw_spins")
+        return a.reshape(self.L, self.L)
+
+    def set_spins(self, src):
+        """Replace the configuration from a numpy array or a CUDA uint8 tensor."""
+        if hasattr(src, "is_cuda") and src.is_cuda:
+            assert src.numel() == self.N and src.is_contiguous()
+            check(lib().sw_set_spins(self._h, ctypes.c_void_p(src.data_ptr()), self.N, 1),
+                  "sw_set_spins")
+            return
+        a = np.ascontiguousarray(np.asarray(src, dtype=np.uint8).reshape(-1))
+        check(lib().sw_set_spins(self._h, a.ctypes.data_as(ctypes.c_void_p), self.N, 0),
+              "sw_set_spins")
+
+    def bonds(self):
+        bp = (self.L + 3) // 4
+        a = np.empty(self.L * bp, dtype=np.uint8)
+        check(lib().sw_bonds(self._h, a.ctypes.data_as(ctypes.c_void_p), a.size, 0), "sw_bonds")
+        return a.reshape(self.L, bp)
+
+    @property
+    def sweep_count(self):
+        v = ctypes.c_uint64()
+        check(lib().sw_get_sweep(self._h, ctypes.byref(v)), "sw_get_sweep")
+        return int(v.value)
+
+    def set_sweep(self, s):
+        check(lib().sw_set_sweep(self._h, int(s)), "sw_set_sweep")
+
+    def info(self):
+        i = sw_info_t()
+        check(lib().sw_info(self._h, ctypes.byref(i)), "sw_info")
+        return {k: getattr(i, k) for k, _ in sw_info_t._fields_}
+
+    @property
+    def handle(self):
+        return self._h
+
+
+def label_bonds(L, bonds_dev, roots_dev, label_bits=32, tile_h=0, stream=None):
+    """Step (2) alone on device buffers (torch tensors): packed bonds in,
+    per-site roots (uint32/int64 tensor of L*L) out."""
+    check(lib().sw_label_bonds(int(L), ctypes.c_void_p(bonds_dev.data_ptr()),
+                               ctypes.c_void_p(roots_dev.data_ptr()), int(label_bits),
+                               int(tile_h), _stream_handle(stream)), "sw_label_bonds")
+
+
+def unpack_bonds(packed, L):
+    """Packed bond lattice (L x ceil(L/4) bytes) -> per-site bits (bit0 right,
+    bit1 down), L x L uint8."""
+    p = np.asarray(packed, dtype=np.uint8).reshape(L, -1)
+    out = np.zeros((L, p.shape[1] * 4), dtype=np.uint8)
+    for k in range(4):
+        out[:, k::4] = (p >> (2 * k)) & 3
+    return out[:, :L]
+
+
+def pack_bonds(b):
+    """Per-site bits (L x L) -> packed bond lattice (L x ceil(L/4))."""
+    b = np.asarray(b, dtype=np.uint8)
+    L = b.shape[0]
+    bp = (L + 3) // 4
+    pad = np.zeros((L, bp * 4), dtype=np.uint8)
+    pad[:, :L] = b & 3
+    out = np.zeros((L, bp), dtype=np.uint8)
+    for k in range(4):
+        out |= pad[:, k::4] << (2 * k)
+    return out

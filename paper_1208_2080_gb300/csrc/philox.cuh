@@ -1,0 +1,58 @@
+// philox.cuh -- device Philox4x32-10 counter-based generator.
+//
+// Written from the published algorithm (Salmon, Moraes, Dror, Shaw,
+// "Parallel random numbers: as easy as 1, 2, 3", SC'11, Sec. 5): ten rounds
+// of two 32x32->64 multiplications whose high halves are xored into the other
+// two counter words together with the round key, the key advancing by two
+// Weyl constants between rounds.  The Swendsen-Wang streams built on it
+// (bonds, new cluster states, initial spins) are the counter layouts of
+// include/sw.h; the same streams are reimplemented independently by the CPU
+// oracle, and tested against cuRAND's device Philox at run time.
+#pragma once
+#include <stdint.h>
+
+namespace swgb {
+
+struct Words4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                uint32_t c3, uint32_t k0, uint32_t k1) {
+  constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+  constexpr uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kMul0, c0), lo0 = kMul0 * c0;
+    const uint32_t hi1 = __umulhi(kMul1, c2), lo1 = kMul1 * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += kWeyl0;
+    k1 += kWeyl1;
+  }
+  return Words4{c0, c1, c2, c3};
+}
+
+// Stream domains (fourth counter word).
+enum : uint32_t { kDomBond = 0, kDomSpin = 1, kDomInit = 2 };
+
+__device__ __forceinline__ Words4 stream4(uint64_t seed, uint64_t idx, uint32_t sweep,
+                                          uint32_t dom) {
+  return philox4x32_10((uint32_t)idx, (uint32_t)(idx >> 32), sweep, dom, (uint32_t)seed,
+                       (uint32_t)(seed >> 32));
+}
+
+// floor(w * q / 2^32): the state a 32-bit word picks.
+__device__ __forceinline__ uint32_t pick_state(uint32_t w, uint32_t q) { return __umulhi(w, q); }
+
+// New state of the cluster whose root (smallest site index) is r.
+__device__ __forceinline__ uint32_t cluster_state(uint64_t seed, uint64_t r, uint32_t sweep,
+                                                  uint32_t q) {
+  return pick_state(stream4(seed, r, sweep, kDomSpin).x, q);
+}
+
+}  // namespace swgb

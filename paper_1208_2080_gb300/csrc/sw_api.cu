@@ -1,0 +1,609 @@
+// sw_api.cu -- C ABI of the single-lattice Swendsen-Wang library (include/sw.h).
+//
+// Host side only: argument checks, device memory layout, launches of the
+// kernels in sw_kernels.cuh on the handle's stream, observable bookkeeping.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/sw.h"
+#include "sw_internal.h"
+#include "sw_kernels.cuh"
+
+using namespace swgb;
+
+// ------------------------------------------------------------------ allocator
+namespace swgb {
+static sw_alloc_fn g_alloc = nullptr;
+static sw_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+
+DeviceAllocator current_allocator() { return DeviceAllocator{g_alloc, g_free, g_alloc_ctx}; }
+
+void* DeviceAllocator::allocate(size_t bytes) const {
+  if (bytes == 0) bytes = 256;
+  if (alloc) return alloc(bytes, ctx);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void DeviceAllocator::release(void* p, size_t bytes) const {
+  if (!p) return;
+  if (bytes == 0) bytes = 256;
+  if (free_fn)
+    free_fn(p, bytes, ctx);
+  else
+    cudaFree(p);
+}
+
+uint32_t bond_threshold(double T) {
+  // p = 1 - exp(-J/T), J = 1: the SW bond probability for H = -J sum delta
+  const double p = -expm1(-1.0 / T);
+  const double t = floor(p * 4294967296.0);
+  if (!(t > 0.0)) return 0u;
+  if (t >= 4294967295.0) return 0xFFFFFFFFu;
+  return (uint32_t)t;
+}
+
+uint32_t pick_tile_h(uint64_t L, uint32_t requested) {
+  if (requested) return requested;
+  if (L <= 32) return 16;
+  if (L <= 256) return 32;
+  return 64;
+}
+
+Lattice make_lattice(uint64_t L, uint32_t th) {
+  Lattice lat;
+  lat.L = L;
+  lat.ntx = (uint32_t)((L + kTW - 1) / kTW);
+  lat.nty = (uint32_t)((L + th - 1) / th);
+  lat.bp = (L + 3) / 4;
+  lat.vec4 = (L % 4 == 0) ? 1u : 0u;
+  lat.ntiles = lat.ntx * lat.nty;
+  return lat;
+}
+
+size_t edge_u16(uint32_t th) { return 2 * (size_t)th + 2 * kTW; }
+size_t bit_words(uint32_t th) { return (th + 31) / 32 + kTW / 32; }
+size_t open_cap(uint32_t th) { return 2 * (size_t)th + 2 * kTW; }
+
+// ---- launch helpers, instantiated for every tile height / label width
+template <int TH, typename LabelT, bool kGiven, bool kRoots>
+static cudaError_t launch_label_t(const Bufs& b, const Lattice& lat, cudaStream_t st) {
+  auto kern = k_label_tile<TH, LabelT, kGiven, kRoots>;
+  const int smem = LabelSmem<TH>::kBytes;
+  static bool configured = false;  // per instantiation; attribute is per function
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  kern<<<lat.ntiles, kThreads, smem, st>>>(b, lat);
+  return cudaGetLastError();
+}
+
+template <int TH, typename LabelT>
+static cudaError_t launch_merge_t(const Bufs& b, const Lattice& lat, cudaStream_t st) {
+  const uint64_t items = (uint64_t)lat.ntiles * (TH + kTW);
+  const uint64_t blocks = (items + kMergeThreads - 1) / kMergeThreads;
+  k_merge<TH, LabelT><<<(unsigned)blocks, kMergeThreads, 0, st>>>(b, lat);
+  return cudaGetLastError();
+}
+
+template <int TH, typename LabelT, bool kRoots>
+static cudaError_t launch_recolor_t(const Bufs& b, const Lattice& lat, LabelT* roots, cudaStream_t st) {
+  k_recolor<TH, LabelT, kRoots><<<lat.ntiles, kThreads, 0, st>>>(b, lat, roots);
+  return cudaGetLastError();
+}
+
+template <typename LabelT>
+static cudaError_t sweep_once_t(uint32_t th, const Bufs& b, const Lattice& lat, cudaStream_t st) {
+  cudaError_t e;
+  switch (th) {
+#define SWGB_CASE(THV)                                                        \
+  case THV:                                                                   \
+    if ((e = launch_label_t<THV, LabelT, false, false>(b, lat, st))) return e; \
+    if ((e = launch_merge_t<THV, LabelT>(b, lat, st))) return e;              \
+    return launch_recolor_t<THV, LabelT, false>(b, lat, nullptr, st);
+    SWGB_CASE(16)
+    SWGB_CASE(32)
+    SWGB_CASE(64)
+#undef SWGB_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_sweep(uint32_t label_bits, uint32_t th, const Bufs& b, const Lattice& lat,
+                         cudaStream_t st) {
+  return label_bits == 64 ? sweep_once_t<uint64_t>(th, b, lat, st)
+                          : sweep_once_t<uint32_t>(th, b, lat, st);
+}
+
+template <typename LabelT>
+static cudaError_t label_given_t(uint32_t th, const Bufs& b, const Lattice& lat, LabelT* roots,
+                                 cudaStream_t st) {
+  cudaError_t e;
+  switch (th) {
+#define SWGB_CASE(THV)                                                      \
+  case THV:                                                                 \
+    if ((e = launch_label_t<THV, LabelT, true, true>(b, lat, st))) return e; \
+    if ((e = launch_merge_t<THV, LabelT>(b, lat, st))) return e;            \
+    return launch_recolor_t<THV, LabelT, true>(b, lat, roots, st);
+    SWGB_CASE(16)
+    SWGB_CASE(32)
+    SWGB_CASE(64)
+#undef SWGB_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_measure(const uint8_t* spin, const Lattice& lat, uint32_t q,
+                           const Bufs& b, cudaStream_t st) {
+  const uint64_t total = ((lat.L + 3) / 4) * lat.L;
+  uint64_t blocks = (total + 255) / 256;
+  if (blocks > 152ull * 16) blocks = 152ull * 16;
+  if (blocks == 0) blocks = 1;
+  k_measure<<<(unsigned)blocks, 256, 0, st>>>(spin, lat, q, b.acc);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
+  k_commit<<<1, 32, 0, st>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(uint8_t* spin, uint64_t N, uint32_t q, uint64_t seed, uint32_t mode,
+                        cudaStream_t st) {
+  if (mode == SW_INIT_ZERO) return cudaMemsetAsync(spin, 0, N, st);
+  const uint64_t nq = (N + 3) / 4;
+  uint64_t blocks = (nq + 255) / 256;
+  if (blocks > 152ull * 32) blocks = 152ull * 32;
+  if (blocks == 0) blocks = 1;
+  k_init_spins<<<(unsigned)blocks, 256, 0, st>>>(spin, N, q, seed);
+  return cudaGetLastError();
+}
+
+}  // namespace swgb
+
+// ------------------------------------------------------------------ handle
+struct sw_sim {
+  sw_params p;
+  uint64_t L = 0, N = 0;
+  uint32_t q = 0, thr = 0, label_bits = 32, th = 64, ring = 1024;
+  Lattice lat{};
+  cudaStream_t stream = nullptr;
+  DeviceAllocator alloc{};
+  std::vector<std::pair<void*, size_t>> blocks;
+  uint64_t dev_bytes = 0;
+  Bufs b{};
+  uint64_t sweep = 0;          // host mirror of ctl[0]
+  uint64_t measured_from = 0;  // oldest configuration whose observables are valid
+  bool pending = true;         // current configuration not measured yet
+  bool measure_on = true;
+  int last_err = SW_OK;
+  int device = 0;
+};
+
+namespace {
+
+int fail(sw_sim* s, int code) {
+  if (s && (code == SW_ERR_CUDA || code == SW_ERR_DEVICE || code == SW_ERR_TIMEOUT)) s->last_err = code;
+  return code;
+}
+
+int cuda_fail(sw_sim* s, cudaError_t e) {
+  (void)e;
+  cudaGetLastError();
+  return fail(s, SW_ERR_CUDA);
+}
+
+void* take(sw_sim* s, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = s->alloc.allocate(bytes);
+  if (p) {
+    s->blocks.emplace_back(p, bytes);
+    s->dev_bytes += bytes;
+  }
+  return p;
+}
+
+void release_all(sw_sim* s) {
+  for (auto& kv : s->blocks) s->alloc.release(kv.first, kv.second);
+  s->blocks.clear();
+  s->dev_bytes = 0;
+}
+
+bool sticky(const sw_sim* s) { return s->last_err != SW_OK; }
+
+// Reads the device error word; maps it onto an error code.
+int check_device(sw_sim* s) {
+  uint32_t err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, s->b.err, sizeof(err), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  if (err & (kErrFind | kErrUnion)) return fail(s, SW_ERR_TIMEOUT);
+  if (err) return fail(s, SW_ERR_DEVICE);
+  return SW_OK;
+}
+
+int measure_current(sw_sim* s) {
+  if (!s->pending) return SW_OK;
+  cudaError_t e = launch_measure(s->b.spin, s->lat, s->q, s->b, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  s->pending = false;
+  return SW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sw_set_allocator(sw_alloc_fn alloc, sw_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return SW_ERR_INVAL;
+  swgb::g_alloc = alloc;
+  swgb::g_free = free_fn;
+  swgb::g_alloc_ctx = ctx;
+  return SW_OK;
+}
+
+int sw_threshold(double T, uint32_t* thr) {
+  if (!thr || !(T > 0.0) || !isfinite(T)) return SW_ERR_INVAL;
+  *thr = bond_threshold(T);
+  return SW_OK;
+}
+
+int sw_create(uint64_t L, uint32_t q, double T, uint64_t seed, sw_sim** out) {
+  sw_params p;
+  memset(&p, 0, sizeof(p));
+  p.L = L;
+  p.q = q;
+  p.T = T;
+  p.seed = seed;
+  return sw_create_ex(&p, out);
+}
+
+int sw_create_ex(const sw_params* prm, sw_sim** out) {
+  if (!prm || !out) return SW_ERR_INVAL;
+  *out = nullptr;
+  const uint64_t L = prm->L;
+  if (L < 2 || L > (1ull << 20) || prm->q < 2 || prm->q > 255 || !(prm->T > 0.0) ||
+      !isfinite(prm->T) || prm->init > SW_INIT_ZERO || prm->store_bonds > 1 || prm->measure > 2)
+    return SW_ERR_INVAL;
+  uint32_t lb = prm->label_bits ? prm->label_bits : (L <= 32768 ? 32u : 64u);
+  if (lb != 32 && lb != 64) return SW_ERR_INVAL;
+  if (lb == 32 && L * L > (1ull << 32)) return SW_ERR_INVAL;
+  const uint32_t th = pick_tile_h(L, prm->tile_h);
+  if (th != 16 && th != 32 && th != 64) return SW_ERR_INVAL;
+  const uint32_t ring = prm->ring ? prm->ring : 1024u;
+
+  sw_sim* s = new (std::nothrow) sw_sim();
+  if (!s) return SW_ERR_NOMEM;
+  s->p = *prm;
+  s->L = L;
+  s->N = L * L;
+  s->q = prm->q;
+  s->thr = bond_threshold(prm->T);
+  s->label_bits = lb;
+  s->th = th;
+  s->ring = ring;
+  s->lat = make_lattice(L, th);
+  s->alloc = current_allocator();
+  s->measure_on = prm->measure != 2;
+  cudaGetDevice(&s->device);
+
+  const uint64_t nt = s->lat.ntiles;
+  Bufs& b = s->b;
+  b.spin = (uint8_t*)take(s, s->N + 16);
+  b.code = (uint16_t*)take(s, s->N * 2 + 16);
+  b.bonds = prm->store_bonds ? (uint8_t*)take(s, L * s->lat.bp + 16) : nullptr;
+  b.T = take(s, s->N * (lb / 8));
+  b.edge = (uint16_t*)take(s, nt * edge_u16(th) * 2);
+  b.ebits = (uint32_t*)take(s, nt * bit_words(th) * 4);
+  b.olist = (uint16_t*)take(s, nt * open_cap(th) * 2);
+  b.ocnt = (uint32_t*)take(s, nt * 4);
+  b.acc = (unsigned long long*)take(s, 8 * 260);
+  b.ring = (unsigned long long*)take(s, (size_t)ring * (2 + s->q) * 8);
+  b.ctl = (unsigned long long*)take(s, 64);
+  b.err = (uint32_t*)take(s, 64);
+  if (!b.spin || !b.code || (prm->store_bonds && !b.bonds) || !b.T || !b.edge || !b.ebits ||
+      !b.olist || !b.ocnt || !b.acc || !b.ring || !b.ctl || !b.err) {
+    release_all(s);
+    delete s;
+    return SW_ERR_NOMEM;
+  }
+  b.seed = prm->seed;
+  b.thr = s->thr;
+  b.q = s->q;
+  b.ring_cap = ring;
+  b.measure = s->measure_on ? 1u : 0u;
+
+  cudaError_t e = cudaSuccess;
+  if (!e) e = cudaMemsetAsync(b.T, 0, s->N * (lb / 8), s->stream);
+  if (!e) e = cudaMemsetAsync(b.acc, 0, 8 * 260, s->stream);
+  if (!e) e = cudaMemsetAsync(b.ring, 0xFF, (size_t)ring * (2 + s->q) * 8, s->stream);
+  if (!e) e = cudaMemsetAsync(b.ctl, 0, 64, s->stream);
+  if (!e) e = cudaMemsetAsync(b.err, 0, 64, s->stream);
+  if (!e) e = cudaMemsetAsync(b.ocnt, 0, nt * 4, s->stream);
+  if (!e) e = launch_init(b.spin, s->N, s->q, prm->seed, prm->init, s->stream);
+  if (!e) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    release_all(s);
+    delete s;
+    return SW_ERR_CUDA;
+  }
+  s->sweep = 0;
+  s->measured_from = 0;
+  s->pending = true;
+  *out = s;
+  return SW_OK;
+}
+
+void sw_destroy(sw_sim* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  release_all(s);
+  delete s;
+}
+
+int sw_bind_stream(sw_sim* s, void* stream) {
+  if (!s) return SW_ERR_INVAL;
+  s->stream = (cudaStream_t)stream;
+  return SW_OK;
+}
+
+int sw_sweep(sw_sim* s, uint64_t n) {
+  if (!s) return SW_ERR_INVAL;
+  if (sticky(s)) return s->last_err;
+  for (uint64_t k = 0; k < n; ++k) {
+    cudaError_t e = launch_sweep(s->label_bits, s->th, s->b, s->lat, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e);
+  }
+  if (n) {
+    s->sweep += n;
+    s->pending = true;
+  }
+  return SW_OK;
+}
+
+int sw_sync(sw_sim* s) {
+  if (!s) return SW_ERR_INVAL;
+  if (sticky(s)) return s->last_err;
+  return check_device(s);
+}
+
+int sw_series(sw_sim* s, uint64_t first, uint64_t count, uint64_t* E, uint64_t* n) {
+  if (!s) return SW_ERR_INVAL;
+  if (sticky(s)) return s->last_err;
+  if (count == 0) return SW_OK;
+  const uint64_t cur = s->sweep;
+  const uint64_t last = first + count - 1;
+  if (last < first || last > cur) return SW_ERR_RANGE;
+  uint64_t oldest = s->measured_from;
+  if (cur + 1 > s->ring && cur + 1 - s->ring > oldest) oldest = cur + 1 - s->ring;
+  if (first < oldest) return SW_ERR_RANGE;
+  if (!s->measure_on && !(first == cur && count == 1)) return SW_ERR_RANGE;
+  if (last == cur) {
+    int rc = measure_current(s);
+    if (rc) return rc;
+  }
+  const size_t rec = 2 + s->q;
+  std::vector<unsigned long long> host(count * rec);
+  // copy the ring window (at most two contiguous pieces)
+  uint64_t done = 0;
+  while (done < count) {
+    const uint64_t c = first + done;
+    const uint64_t slot = c % s->ring;
+    uint64_t run = s->ring - slot;
+    if (run > count - done) run = count - done;
+    cudaError_t e = cudaMemcpyAsync(host.data() + done * rec, s->b.ring + slot * rec,
+                                    run * rec * 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e);
+    done += run;
+  }
+  int rc = check_device(s);
+  if (rc) return rc;
+  for (uint64_t k = 0; k < count; ++k) {
+    const unsigned long long* r = host.data() + k * rec;
+    if (r[0] != first + k) return SW_ERR_RANGE;
+    if (E) E[k] = r[1];
+    if (n)
+      for (uint32_t j = 0; j < s->q; ++j) n[k * s->q + j] = r[2 + j];
+  }
+  return SW_OK;
+}
+
+int sw_measure(sw_sim* s, sw_obs* out) {
+  if (!s || !out) return SW_ERR_INVAL;
+  memset(out, 0, sizeof(*out));
+  uint64_t E = 0;
+  std::vector<uint64_t> n(s->q);
+  const uint64_t cur = s->sweep;
+  // sw_series would refuse when measurement is off; measure directly then
+  if (!s->measure_on) {
+    if (sticky(s)) return s->last_err;
+    s->pending = true;
+    int rc = measure_current(s);
+    if (rc) return rc;
+    const size_t rec = 2 + s->q;
+    std::vector<unsigned long long> host(rec);
+    cudaError_t e = cudaMemcpyAsync(host.data(), s->b.ring + (cur % s->ring) * rec, rec * 8,
+                                    cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e);
+    rc = check_device(s);
+    if (rc) return rc;
+    if (host[0] != cur) return fail(s, SW_ERR_DEVICE);
+    E = host[1];
+    for (uint32_t j = 0; j < s->q; ++j) n[j] = host[2 + j];
+  } else {
+    int rc = sw_series(s, cur, 1, &E, n.data());
+    if (rc) return rc;
+  }
+  out->config = cur;
+  out->E_sat = E;
+  out->q = s->q;
+  for (uint32_t j = 0; j < s->q; ++j) out->n[j] = n[j];
+  return SW_OK;
+}
+
+int sw_spins(sw_sim* s, uint8_t* dst, uint64_t n, int dst_on_device) {
+  if (!s || !dst || n != s->N) return SW_ERR_INVAL;
+  if (sticky(s)) return s->last_err;
+  cudaError_t e = cudaMemcpyAsync(dst, s->b.spin, s->N,
+                                  dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  if (!dst_on_device) return check_device(s);
+  return SW_OK;
+}
+
+int sw_set_spins(sw_sim* s, const uint8_t* src, uint64_t n, int src_on_device) {
+  if (!s || !src || n != s->N) return SW_ERR_INVAL;
+  if (sticky(s)) return s->last_err;
+  if (!src_on_device) {
+    for (uint64_t i = 0; i < n; ++i)
+      if (src[i] >= s->q) return SW_ERR_INVAL;
+  }
+  cudaError_t e = cudaMemcpyAsync(s->b.spin, src, s->N,
+                                  src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  if (!src_on_device) {
+    e = cudaStreamSynchronize(s->stream);  // the caller may reuse src on return
+    if (e != cudaSuccess) return cuda_fail(s, e);
+  }
+  s->pending = true;
+  s->measured_from = s->sweep;
+  return SW_OK;
+}
+
+int sw_bonds(sw_sim* s, uint8_t* dst, uint64_t nbytes, int dst_on_device) {
+  if (!s || !dst) return SW_ERR_INVAL;
+  if (!s->b.bonds) return SW_ERR_STATE;
+  if (nbytes != s->L * s->lat.bp) return SW_ERR_INVAL;
+  if (sticky(s)) return s->last_err;
+  cudaError_t e = cudaMemcpyAsync(dst, s->b.bonds, nbytes,
+                                  dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  if (!dst_on_device) return check_device(s);
+  return SW_OK;
+}
+
+int sw_get_sweep(const sw_sim* s, uint64_t* sweep) {
+  if (!s || !sweep) return SW_ERR_INVAL;
+  *sweep = s->sweep;
+  return SW_OK;
+}
+
+int sw_set_sweep(sw_sim* s, uint64_t sweep) {
+  if (!s) return SW_ERR_INVAL;
+  if (sticky(s)) return s->last_err;
+  unsigned long long v = sweep;
+  cudaError_t e = cudaMemcpyAsync(s->b.ctl, &v, sizeof(v), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  s->sweep = sweep;
+  s->measured_from = sweep;
+  s->pending = true;
+  return SW_OK;
+}
+
+int sw_info(const sw_sim* s, sw_info_t* out) {
+  if (!s || !out) return SW_ERR_INVAL;
+  out->L = s->L;
+  out->q = s->q;
+  out->thr = s->thr;
+  out->label_bits = s->label_bits;
+  out->tile_w = kTW;
+  out->tile_h = s->th;
+  out->ring = s->ring;
+  out->device_bytes = s->dev_bytes;
+  out->tiles = s->lat.ntiles;
+  return SW_OK;
+}
+
+int sw_last_error(const sw_sim* s) { return s ? s->last_err : SW_ERR_INVAL; }
+
+const char* sw_strerror(int code) {
+  switch (code) {
+    case SW_OK: return "ok";
+    case SW_ERR_INVAL: return "invalid argument";
+    case SW_ERR_NOMEM: return "out of memory";
+    case SW_ERR_CUDA: return "CUDA runtime error";
+    case SW_ERR_TIMEOUT: return "bounded device loop hit its iteration cap";
+    case SW_ERR_STATE: return "call not valid in this state";
+    case SW_ERR_DEVICE: return "device-side consistency check failed";
+    case SW_ERR_RANGE: return "observables not held for the requested configurations";
+    default: return "unknown error";
+  }
+}
+
+int sw_label_bonds(uint64_t L, const uint8_t* bonds, void* roots, uint32_t label_bits,
+                   uint32_t tile_h, void* stream) {
+  if (L < 2 || L > (1ull << 20) || !bonds || !roots) return SW_ERR_INVAL;
+  if (label_bits != 32 && label_bits != 64) return SW_ERR_INVAL;
+  if (label_bits == 32 && L * L > (1ull << 32)) return SW_ERR_INVAL;
+  const uint32_t th = pick_tile_h(L, tile_h);
+  if (th != 16 && th != 32 && th != 64) return SW_ERR_INVAL;
+  const Lattice lat = make_lattice(L, th);
+  const DeviceAllocator al = current_allocator();
+  const uint64_t N = L * L, nt = lat.ntiles;
+  struct Blk { void* p; size_t n; };
+  std::vector<Blk> blk;
+  auto get = [&](size_t n) -> void* {
+    n = (n + 255) & ~(size_t)255;
+    void* p = al.allocate(n);
+    if (p) blk.push_back({p, n});
+    return p;
+  };
+  Bufs b{};
+  b.bonds = const_cast<uint8_t*>(bonds);
+  b.code = (uint16_t*)get(N * 2 + 16);
+  b.T = get(N * (label_bits / 8));
+  b.edge = (uint16_t*)get(nt * edge_u16(th) * 2);
+  b.ebits = (uint32_t*)get(nt * bit_words(th) * 4);
+  b.olist = (uint16_t*)get(nt * open_cap(th) * 2);
+  b.ocnt = (uint32_t*)get(nt * 4);
+  b.ctl = (unsigned long long*)get(64);
+  b.err = (uint32_t*)get(64);
+  b.q = 2;
+  b.measure = 0;
+  int rc = SW_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!b.code || !b.T || !b.edge || !b.ebits || !b.olist || !b.ocnt || !b.ctl || !b.err) {
+    rc = SW_ERR_NOMEM;
+  } else {
+    cudaError_t e = cudaMemsetAsync(b.ctl, 0, 64, st);
+    if (!e) e = cudaMemsetAsync(b.err, 0, 64, st);
+    if (!e) e = cudaMemsetAsync(b.T, 0, N * (label_bits / 8), st);
+    if (!e)
+      e = label_bits == 64 ? label_given_t<uint64_t>(th, b, lat, (uint64_t*)roots, st)
+                           : label_given_t<uint32_t>(th, b, lat, (uint32_t*)roots, st);
+    uint32_t err = 0;
+    if (!e) e = cudaMemcpyAsync(&err, b.err, 4, cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      rc = SW_ERR_CUDA;
+    } else if (err & (kErrFind | kErrUnion)) {
+      rc = SW_ERR_TIMEOUT;
+    } else if (err) {
+      rc = SW_ERR_DEVICE;
+    }
+  }
+  cudaStreamSynchronize(st);
+  for (auto& x : blk) al.release(x.p, x.n);
+  return rc;
+}
+
+}  // extern "C"

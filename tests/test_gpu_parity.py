@@ -1,0 +1,207 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bit-exact on every integer output: initial spins, the packed bond lattice,
+cluster roots, spins after every sweep, per-configuration E_sat and n[s].
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1208_2080_gb300 as sw
+
+pytestmark = pytest.mark.gpu
+
+TILE_HS = [16, 32, 64]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+# ---- initial spins: pins the GPU Philox against the oracle's ----------------
+@pytest.mark.parametrize("L", [2, 3, 5, 17, 64, 100, 129, 256, 301])
+def test_init_spins(L):
+    q, seed = 5, 1234 + L
+    with sw.Sim(L, q, 1.0, seed) as s:
+        assert np.array_equal(s.spins(), oracle.init_spins(L, q, seed))
+
+
+# ---- step (1): bonds ---------------------------------------------------------
+@pytest.mark.parametrize("L", [2, 3, 4, 7, 64, 127, 128, 130, 257])
+@pytest.mark.parametrize("q", [2, 3])
+def test_bonds_bit_exact(L, q):
+    T, seed = sw.tc(q), 99 + L
+    with sw.Sim(L, q, T, seed, store_bonds=True) as s:
+        s0 = s.spins()
+        s.sweep(1)
+        got = sw.unpack_bonds(s.bonds(), L)
+        ref = oracle.bonds(s0, T, seed, 0)
+        assert np.array_equal(got, ref)
+        s1 = s.spins()
+        s.sweep(1)
+        assert np.array_equal(sw.unpack_bonds(s.bonds(), L), oracle.bonds(s1, T, seed, 1))
+
+
+# ---- step (2): labelling of given bond lattices ------------------------------
+def _label_gpu(b, label_bits, tile_h):
+    torch = _torch()
+    L = b.shape[0]
+    packed = torch.from_numpy(sw.pack_bonds(b).reshape(-1).copy()).cuda()
+    dt = torch.int32 if label_bits == 32 else torch.int64
+    roots = torch.empty(L * L, dtype=dt, device="cuda")
+    sw.label_bonds(L, packed, roots, label_bits=label_bits, tile_h=tile_h)
+    torch.cuda.synchronize()
+    r = roots.cpu().numpy()
+    return (r.view(np.uint32) if label_bits == 32 else r.view(np.uint64)).reshape(L, L)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4, 5, 9, 16, 17, 31, 33, 63, 64, 65, 127, 128, 129, 200, 256])
+@pytest.mark.parametrize("tile_h", TILE_HS)
+def test_label_matches_hk(L, tile_h):
+    rng = np.random.default_rng(L * 7 + tile_h)
+    for density in [0.0, 1.0, 0.3, 0.5, 0.58, 0.7, 0.9]:
+        b = (rng.random((L, L)) < density).astype(np.uint8) | \
+            ((rng.random((L, L)) < density).astype(np.uint8) << 1)
+        ref = oracle.label(b)
+        for bits in (32, 64):
+            assert np.array_equal(_label_gpu(b, bits, tile_h), ref), (L, tile_h, density, bits)
+
+
+def test_label_structured():
+    L = 300
+    # long horizontal snake that crosses every tile edge and wraps
+    b = np.zeros((L, L), np.uint8)
+    b[::2, :] |= 1
+    b[:, L - 1] |= 2
+    b[:, 0] |= 2
+    ref = oracle.label(b)
+    for th in TILE_HS:
+        assert np.array_equal(_label_gpu(b, 32, th), ref)
+    # checkerboard of isolated 2x2 blocks straddling tile edges
+    b = np.zeros((L, L), np.uint8)
+    b[1::2, 1::2] = 3
+    ref = oracle.label(b)
+    assert np.array_equal(_label_gpu(b, 64, 64), ref)
+
+
+# ---- whole sweeps ------------------------------------------------------------
+CASES = [
+    (2, 2, None), (3, 3, None), (5, 2, None), (8, 4, None), (17, 3, None), (31, 5, None),
+    (64, 2, None), (100, 8, None), (128, 2, None), (129, 3, None), (200, 255, None),
+    (257, 2, None), (64, 2, 0.05), (64, 3, 1e6), (96, 2, 0.5), (160, 4, 3.0),
+]
+
+
+@pytest.mark.parametrize("L,q,T", CASES)
+def test_sweeps_bit_exact(L, q, T):
+    T = sw.tc(q) if T is None else T
+    seed, n = 7 * L + q, 12
+    with sw.Sim(L, q, T, seed) as s:
+        s.sweep(n)
+        got = s.spins()
+        E, nn = s.series(0, n + 1)
+    ref, refE, refn = oracle.run(L, q, T, seed, n)
+    assert np.array_equal(got, ref)
+    E0, n0 = oracle.measure(oracle.init_spins(L, q, seed), q)
+    assert E[0] == E0 and np.array_equal(nn[0], n0)
+    assert np.array_equal(E[1:], refE)
+    assert np.array_equal(nn[1:], refn)
+
+
+@pytest.mark.parametrize("L", [96, 250])
+def test_results_independent_of_tile_and_label_width(L):
+    q, T, seed, n = 3, sw.tc(3), 4242, 6
+    outs = []
+    for th in TILE_HS:
+        for bits in (32, 64):
+            with sw.Sim(L, q, T, seed, tile_h=th, label_bits=bits) as s:
+                s.sweep(n)
+                outs.append((s.spins(), s.series(0, n + 1)))
+    for sp, (E, nn) in outs[1:]:
+        assert np.array_equal(sp, outs[0][0])
+        assert np.array_equal(E, outs[0][1][0]) and np.array_equal(nn, outs[0][1][1])
+
+
+def test_config_ising_L256_1000_sweeps():
+    """q=2, L=256, T_c, random start, 1000 sweeps: every configuration's E_sat
+    and n[s] bit-exact, final spins bit-exact."""
+    L, q, T, seed, n = 256, 2, sw.tc(2), 1, 1000
+    with sw.Sim(L, q, T, seed, ring=2048) as s:
+        s.sweep(n)
+        got = s.spins()
+        E, nn = s.series(1, n)
+    ref, refE, refn = oracle.run(L, q, T, seed, n)
+    assert np.array_equal(E, refE) and np.array_equal(nn, refn)
+    assert np.array_equal(got, ref)
+
+
+def test_zero_start_and_resume():
+    L, q, T, seed = 130, 2, sw.tc(2), 5
+    with sw.Sim(L, q, T, seed, init="zero") as a:
+        assert not a.spins().any()
+        a.sweep(4)
+        mid, t = a.spins(), a.sweep_count
+        a.sweep(5)
+        end = a.spins()
+    ref, _, _ = oracle.run(L, q, T, seed, 9, spins=np.zeros((L, L), np.uint8))
+    assert np.array_equal(end, ref)
+    with sw.Sim(L, q, T, seed) as b:  # different start; resume from the saved state
+        b.set_spins(mid)
+        b.set_sweep(t)
+        b.sweep(5)
+        assert np.array_equal(b.spins(), end)
+
+
+def test_measurement_off_gives_same_chain():
+    L, q, T, seed = 140, 3, sw.tc(3), 11
+    with sw.Sim(L, q, T, seed) as a, sw.Sim(L, q, T, seed, measure=False) as b:
+        a.sweep(7)
+        b.sweep(7)
+        assert np.array_equal(a.spins(), b.spins())
+        assert a.measure()[0] == b.measure()[0]
+        with pytest.raises(sw.SwError):
+            b.series(0, 3)
+
+
+def test_device_spin_io():
+    torch = _torch()
+    L, q, T, seed = 128, 4, sw.tc(4), 3
+    with sw.Sim(L, q, T, seed) as s:
+        dev = torch.zeros(L * L, dtype=torch.uint8, device="cuda")
+        s.spins(out=dev)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev.cpu().numpy().reshape(L, L), oracle.init_spins(L, q, seed))
+        z = torch.zeros(L * L, dtype=torch.uint8, device="cuda")
+        s.set_spins(z)
+        s.sweep(2)
+        ref, _, _ = oracle.run(L, q, T, seed, 2, spins=np.zeros((L, L), np.uint8))
+        assert np.array_equal(s.spins(), ref)
+
+
+def test_ring_window_and_errors():
+    L, q, T = 64, 2, sw.tc(2)
+    with sw.Sim(L, q, T, 1, ring=8) as s:
+        s.sweep(20)
+        s.series(13, 8)
+        with pytest.raises(sw.SwError) as e:
+            s.series(12, 9)
+        assert e.value.code == sw._binding.SW_ERR_RANGE
+        with pytest.raises(sw.SwError):
+            s.set_spins(np.full((L, L), 2, np.uint8))  # state >= q
+    with pytest.raises(sw.SwError):
+        sw.Sim(1, 2, 1.0, 0)
+    with pytest.raises(sw.SwError):
+        sw.Sim(8, 256, 1.0, 0)
+    with pytest.raises(sw.SwError):
+        sw.Sim(8, 2, 0.0, 0)
+
+
+def test_repeatable():
+    L, q, T = 512, 2, sw.tc(2)
+    out = []
+    for _ in range(3):
+        with sw.Sim(L, q, T, 77) as s:
+            s.sweep(10)
+            out.append(s.spins())
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])

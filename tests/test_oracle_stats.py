@@ -72,13 +72,15 @@ def test_chain_statistics_catch_a_wrong_probability():
     assert abs(m - e1) > 5 * s
 
 
-@pytest.mark.parametrize("q", [2, 3])
-def test_critical_energy_baxter(q):
-    """-E_sat/N at T_c approaches -(1+1/sqrt q) (Baxter); at L=128 the
-    finite-size shift is well below the 0.01 tolerance used here."""
+@pytest.mark.parametrize("q,tol", [(2, 0.006), (3, 0.025)])
+def test_critical_energy_baxter(q, tol):
+    """-E_sat/N at T_c approaches -(1+1/sqrt q) (Baxter).  The finite-size
+    shift decays as L^((alpha-1)/nu): 1/L for q=2 (about 0.004 at L=128) and
+    L^-0.8 for q=3 (about 0.013); the tolerances leave room for both, while a
+    wrong bond probability moves u by O(0.1)."""
     L = 128
     T = oracle.tc(q)
     E, _ = _chain(L, q, T, seed=900 + q, n=400, burn=100)
     u = -E / (L * L)
     m, s = _batch_mean(u, nb=20)
-    assert abs(m + (1 + 1 / np.sqrt(q))) < 5 * s + 0.01
+    assert abs(m + (1 + 1 / np.sqrt(q))) < 5 * s + tol
