@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the Swendsen-Wang sweep on one GB300 (one JSON line).
+
+Workload (default): q = 2 (Ising), L = 65536 (4.29e9 sites), T = T_c =
+1/ln(1+sqrt 2), all-zero start, uint64 cluster labels -- the production-size
+configuration of Table 1 / the abstract (37.3 spin flips/ns on 256 M2050).
+A step is one full SW sweep (bonds, labelling, recolouring, fused E/M
+measurement).  W warm-up sweeps, then K timed sweeps; with the defaults
+(W=20, K=80) the run covers exactly the 100 sweeps of that configuration.
+
+Metric: spin updates per ns = N * K / device time.  The timed region holds
+only the library's kernels (inputs resident in HBM, every buffer far larger
+than the 126 MB L2, so no flush is needed).  `e2e` repeats the metric through
+the public API with host buffers: each step uploads the configuration from
+pinned host memory (sw_set_spins), sweeps once and reads the observables
+back (sw_measure).  `roofline` reports the dominant kernel's achieved HBM
+bandwidth from the library's per-launch CUDA events; `cpu_baseline` times the
+CPU oracle on a bounded sample.
+
+--impl reference times the CPU oracle (the only reference implementation of
+this paper's method) as the reference arm, on rank 0.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SW spin updates/ns at q=2, T_c, L=65536 (update + measurement)"
+UNIT = "spin updates/ns"
+PAPER_UPDATE_MEASURE = 33.85  # Table 1, L=65536, 256x Tesla M2050, update + measurement
+# Algorithmic HBM bytes per site moved by each kernel of a sweep in this
+# design: k_label_tile reads the uint8 spin and writes the 16-bit site code;
+# k_recolor reads the code and writes the spin.  O(1/tile) halo and edge
+# terms are left out.
+ALG_BYTES_PER_SITE = {"k_label_tile": 3.0, "k_merge": 0.0, "k_recolor": 3.0}
+PHASES = ["k_label_tile", "k_merge", "k_recolor"]
+THROTTLE = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=5)
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(THROTTLE, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        mhz.sort()
+        return {"sm_mhz": mhz[len(mhz) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("sw_kernels.cuh", "philox.cuh"):
+        with open(os.path.join(ROOT, "paper_1208_2080_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, L):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[kernel]
+        if e.get("source_hash") != _kernel_hash():
+            return None
+        return float(e["bytes_per_site"]) * L * L
+    except Exception:
+        return None
+
+
+def cpu_baseline(seconds=15.0, L=8192):
+    """The oracle, as it stands, single-threaded on a bounded sample: q=2,
+    T_c, L x L from the init stream, as many sweeps as fit in ~`seconds`."""
+    import numpy as np
+    import oracle
+    T = oracle.tc(2)
+    s = oracle.init_spins(L, 2, 5).reshape(-1).copy()
+    t0 = time.perf_counter()
+    oracle.run(L, 2, T, 5, 1, spins=s, sweep0=0, series=False)
+    one = time.perf_counter() - t0
+    n = max(1, int(seconds / max(one, 1e-3)) - 1)
+    t0 = time.perf_counter()
+    oracle.run(L, 2, T, 5, n, spins=s, sweep0=1, series=False)
+    dt = time.perf_counter() - t0
+    del np
+    return {"value": L * L * n / (dt * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"q=2, T_c, L={L} random start, {n} sweeps (after 1 untimed), "
+                      f"single-threaded C oracle, {dt:.1f} s"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    L = args.ref_L
+    T = oracle.tc(2)
+    s = np.zeros(L * L, dtype=np.uint8)
+    for k in range(args.warmup):
+        s, _, _ = oracle.run(L, 2, T, 5, 1, spins=s, sweep0=k, series=False)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        s, _, _ = oracle.run(L, 2, T, 5, 1, spins=s, sweep0=args.warmup + k, series=False)
+    dt = time.perf_counter() - t0
+    value = L * L * args.steps / (dt * 1e9)
+    sample = (f"each step one oracle sweep of a q=2, T_c, L={L} lattice (all-zero start), "
+              f"single-threaded C oracle")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": f"q=2 Ising at T_c, all-zero start; oracle sample L={L} "
+                               f"(bench workload L=65536)", "L": L, "q": 2},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_1208_2080_gb300 as sw
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    L, q = args.L, 2
+    N = L * L
+    T = sw.tc(q)
+    seed = 5 + rank
+    sim = sw.Sim(L, q, T, seed, init="zero", label_bits=args.label_bits)
+    info = sim.info()
+    stream = torch.cuda.current_stream()
+    sim.sweep(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        sim.profile(True)
+        ev0.record(stream)
+        sim.sweep(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    phase_ms, phase_n = sim.profile_read()
+    sim.profile(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    E, n, cfg = sim.measure()
+    assert int(n.sum()) == N and 0 <= E <= 2 * N, "observables out of range"
+    value = N * args.steps * world / (ms * 1e6)
+
+    # update only (Table 1's other column): same chain with measurement off
+    upd = None
+    if args.update_only_steps > 0:
+        spins_dev = torch.empty(N, dtype=torch.uint8, device="cuda")
+        sim.spins(out=spins_dev)
+        cur = sim.sweep_count
+        sim.close()
+        sim = None
+        torch.cuda.empty_cache()
+        sim2 = sw.Sim(L, q, T, seed, measure=False, label_bits=args.label_bits)
+        sim2.set_spins(spins_dev)
+        sim2.set_sweep(cur)
+        del spins_dev
+        sim2.sweep(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim2.sweep(args.update_only_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        upd = N * args.update_only_steps / (e0.elapsed_time(e1) * 1e6)
+        sim = sim2
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        host = torch.empty(N, dtype=torch.uint8, pin_memory=True)
+        dev_tmp = torch.empty(N, dtype=torch.uint8, device="cuda")
+        sim.spins(out=dev_tmp)
+        host.copy_(dev_tmp)
+        del dev_tmp
+        torch.cuda.empty_cache()
+        hnp = host.numpy()
+        sim.set_spins(hnp)
+        sim.sweep(1)
+        sim.measure()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sim.set_spins(hnp)
+            sim.sweep(1)
+            sim.measure()
+        dt = time.perf_counter() - t0
+        e2e = {"value": N * args.e2e_steps * world / (dt * 1e9), "unit": UNIT,
+               "h2d_bytes_per_step": N, "d2h_bytes_per_step": 8 * (2 + q),
+               "steps": args.e2e_steps}
+
+    if rank != 0:
+        return 0
+    peak, peak_kind = _peaks()
+    avg = [m / max(c, 1) for m, c in zip(phase_ms, phase_n)]
+    dom = max(range(3), key=lambda k: phase_ms[k])
+    name = PHASES[dom]
+    alg = ALG_BYTES_PER_SITE[name] * N
+    achieved = alg / (avg[dom] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": _traffic(name, L),
+            "alg_bytes_per_launch": alg, "avg_launch_ms": avg[dom],
+            "phase_ms_per_sweep": {PHASES[k]: avg[k] for k in range(3)}}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": value / PAPER_UPDATE_MEASURE, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": f"q=2 Ising, L={L}, T=T_c, all-zero start, "
+                               f"uint{info['label_bits']} labels, sweeps {args.warmup}.."
+                               f"{args.warmup + args.steps - 1}",
+                   "L": L, "q": q, "tile": f"{info['tile_w']}x{info['tile_h']}",
+                   "l2": "inputs larger than L2 (4 GiB spins, 8 GiB codes at L=65536)",
+                   "replicas": world},
+        "gpu_launches": 3 * args.steps,
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "update_only": {"value": upd, "unit": UNIT, "steps": args.update_only_steps}
+        if upd is not None else None,
+        "observables_last": {"config": cfg, "E_sat": E, "n": [int(x) for x in n]},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=80)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=65536, help="lattice size (default: the workload)")
+    ap.add_argument("--label-bits", type=int, default=0, help="0 = auto (64 above L=32768)")
+    ap.add_argument("--ref-L", type=int, default=4096, help="oracle sample size per reference step")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--update-only-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    return run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -84,7 +84,7 @@ typedef struct {
                            width of the global cluster labels (site indices) */
   double T;             /* temperature in units of J, finite, > 0 */
   uint64_t seed;        /* Philox key */
-  uint32_t tile_h;      /* labelling tile height: 0 = auto, or 16/32/64/128
+  uint32_t tile_h;      /* labelling tile height: 0 = auto, or 16, 32 or 64
                            (tile width is 128 sites); results do not depend
                            on it */
   uint32_t ring;        /* observable ring capacity in configurations,
@@ -137,8 +137,11 @@ int sw_series(sw_sim *sim, uint64_t first, uint64_t count, uint64_t *E,
 /* Copy the L*L spins out to dst (host, or device if dst_on_device).
  * n must equal L*L.  Synchronises for a host destination. */
 int sw_spins(sw_sim *sim, uint8_t *dst, uint64_t n, int dst_on_device);
-/* Replace the configuration (values must be < q; checked on the host for
- * host sources).  The sweep counter is unchanged. */
+/* Replace the configuration from host or device memory.  Values must be
+ * < q: they are checked on the device after the copy; on failure the call
+ * returns SW_ERR_INVAL and the handle refuses to sweep (SW_ERR_STATE) until
+ * a valid configuration is set.  The sweep counter is unchanged; the call
+ * synchronises the handle's stream (the caller may reuse src on return). */
 int sw_set_spins(sw_sim *sim, const uint8_t *src, uint64_t n,
                  int src_on_device);
 
@@ -180,6 +183,15 @@ int sw_threshold(double T, uint32_t *thr);
  * released before return; runs on `stream` and synchronises it. */
 int sw_label_bonds(uint64_t L, const uint8_t *bonds, void *roots,
                    uint32_t label_bits, uint32_t tile_h, void *stream);
+
+/* Per-kernel timing with CUDA events recorded on the handle's stream around
+ * each launch of a sweep (bond+tile labelling, boundary merge, recolour),
+ * for profiling the hot path from the caller's side.  enable = 1 starts
+ * recording (clearing earlier totals), 0 stops.  sw_profile_read
+ * synchronises and returns, per phase, the summed milliseconds and the
+ * number of launches since recording started (arrays of `nphase` <= 3). */
+int sw_profile(sw_sim *sim, int enable);
+int sw_profile_read(sw_sim *sim, double *ms, uint64_t *launches, int nphase);
 
 /* Name of an error code. */
 const char *sw_strerror(int code);

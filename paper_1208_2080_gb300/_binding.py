@@ -30,7 +30,7 @@ EXPORTS = [
     "sw_set_allocator", "sw_create", "sw_create_ex", "sw_destroy", "sw_bind_stream", "sw_sweep",
     "sw_measure", "sw_series", "sw_spins", "sw_set_spins", "sw_bonds", "sw_get_sweep",
     "sw_set_sweep", "sw_sync", "sw_info", "sw_threshold", "sw_label_bonds", "sw_strerror",
-    "sw_last_error",
+    "sw_last_error", "sw_profile", "sw_profile_read",
 ]
 
 
@@ -98,6 +98,8 @@ def lib():
         "sw_label_bonds": (i32, [u64, vp, vp, u32, u32, vp]),
         "sw_strerror": (ctypes.c_char_p, [i32]),
         "sw_last_error": (i32, [vp]),
+        "sw_profile": (i32, [vp, i32]),
+        "sw_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), u64p, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -266,6 +268,16 @@ class Sim:
         i = sw_info_t()
         check(lib().sw_info(self._h, ctypes.byref(i)), "sw_info")
         return {k: getattr(i, k) for k, _ in sw_info_t._fields_}
+
+    def profile(self, enable=True):
+        check(lib().sw_profile(self._h, 1 if enable else 0), "sw_profile")
+
+    def profile_read(self):
+        """(ms[3], launches[3]) per phase: tile labelling, boundary merge, recolour."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_uint64 * 3)()
+        check(lib().sw_profile_read(self._h, ms, n, 3), "sw_profile_read")
+        return list(ms), list(n)
 
     @property
     def handle(self):

@@ -123,6 +123,37 @@ static cudaError_t sweep_once_t(uint32_t th, const Bufs& b, const Lattice& lat, 
   }
 }
 
+// The three launches of one sweep; ev (4 events or null) are recorded
+// before, between and after them.
+template <typename LabelT>
+static cudaError_t sweep_once_ev_t(uint32_t th, const Bufs& b, const Lattice& lat, cudaStream_t st,
+                                   cudaEvent_t* ev) {
+  cudaError_t e;
+  switch (th) {
+#define SWGB_CASE(THV)                                                        \
+  case THV:                                                                   \
+    if ((e = cudaEventRecord(ev[0], st))) return e;                           \
+    if ((e = launch_label_t<THV, LabelT, false, false>(b, lat, st))) return e; \
+    if ((e = cudaEventRecord(ev[1], st))) return e;                           \
+    if ((e = launch_merge_t<THV, LabelT>(b, lat, st))) return e;              \
+    if ((e = cudaEventRecord(ev[2], st))) return e;                           \
+    if ((e = launch_recolor_t<THV, LabelT, false>(b, lat, nullptr, st))) return e; \
+    return cudaEventRecord(ev[3], st);
+    SWGB_CASE(16)
+    SWGB_CASE(32)
+    SWGB_CASE(64)
+#undef SWGB_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_sweep_events(uint32_t label_bits, uint32_t th, const Bufs& b, const Lattice& lat,
+                                cudaStream_t st, cudaEvent_t* ev) {
+  return label_bits == 64 ? sweep_once_ev_t<uint64_t>(th, b, lat, st, ev)
+                          : sweep_once_ev_t<uint32_t>(th, b, lat, st, ev);
+}
+
 cudaError_t launch_sweep(uint32_t label_bits, uint32_t th, const Bufs& b, const Lattice& lat,
                          cudaStream_t st) {
   return label_bits == 64 ? sweep_once_t<uint64_t>(th, b, lat, st)
@@ -191,6 +222,13 @@ struct sw_sim {
   bool measure_on = true;
   int last_err = SW_OK;
   int device = 0;
+  bool spins_invalid = false;  // last sw_set_spins was rejected
+  // per-phase event timing (sw_profile)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;   // free events
+  std::vector<cudaEvent_t> ev_used;   // 4 per profiled sweep, in order
+  double prof_ms[3] = {0, 0, 0};
+  uint64_t prof_launches[3] = {0, 0, 0};
 };
 
 namespace {
@@ -216,7 +254,44 @@ void* take(sw_sim* s, size_t bytes) {
   return p;
 }
 
+cudaEvent_t get_event(sw_sim* s) {
+  if (!s->ev_pool.empty()) {
+    cudaEvent_t e = s->ev_pool.back();
+    s->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Folds recorded event quads into the per-phase totals (after a sync).
+int drain_events(sw_sim* s) {
+  for (size_t k = 0; k + 3 < s->ev_used.size(); k += 4) {
+    for (int ph = 0; ph < 3; ++ph) {
+      float ms = 0.f;
+      cudaError_t e = cudaEventElapsedTime(&ms, s->ev_used[k + ph], s->ev_used[k + ph + 1]);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SW_ERR_CUDA;
+      }
+      s->prof_ms[ph] += ms;
+      s->prof_launches[ph] += 1;
+    }
+  }
+  for (cudaEvent_t e : s->ev_used) s->ev_pool.push_back(e);
+  s->ev_used.clear();
+  return SW_OK;
+}
+
 void release_all(sw_sim* s) {
+  for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : s->ev_used) cudaEventDestroy(e);
+  s->ev_pool.clear();
+  s->ev_used.clear();
   for (auto& kv : s->blocks) s->alloc.release(kv.first, kv.second);
   s->blocks.clear();
   s->dev_bytes = 0;
@@ -364,8 +439,20 @@ int sw_bind_stream(sw_sim* s, void* stream) {
 int sw_sweep(sw_sim* s, uint64_t n) {
   if (!s) return SW_ERR_INVAL;
   if (sticky(s)) return s->last_err;
+  if (s->spins_invalid) return SW_ERR_STATE;
   for (uint64_t k = 0; k < n; ++k) {
-    cudaError_t e = launch_sweep(s->label_bits, s->th, s->b, s->lat, s->stream);
+    cudaError_t e;
+    if (s->profiling) {
+      cudaEvent_t ev[4];
+      for (int j = 0; j < 4; ++j) {
+        ev[j] = get_event(s);
+        if (!ev[j]) return fail(s, SW_ERR_CUDA);
+        s->ev_used.push_back(ev[j]);
+      }
+      e = launch_sweep_events(s->label_bits, s->th, s->b, s->lat, s->stream, ev);
+    } else {
+      e = launch_sweep(s->label_bits, s->th, s->b, s->lat, s->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(s, e);
   }
   if (n) {
@@ -469,20 +556,59 @@ int sw_spins(sw_sim* s, uint8_t* dst, uint64_t n, int dst_on_device) {
 int sw_set_spins(sw_sim* s, const uint8_t* src, uint64_t n, int src_on_device) {
   if (!s || !src || n != s->N) return SW_ERR_INVAL;
   if (sticky(s)) return s->last_err;
-  if (!src_on_device) {
-    for (uint64_t i = 0; i < n; ++i)
-      if (src[i] >= s->q) return SW_ERR_INVAL;
-  }
   cudaError_t e = cudaMemcpyAsync(s->b.spin, src, s->N,
                                   src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                   s->stream);
-  if (e != cudaSuccess) return cuda_fail(s, e);
-  if (!src_on_device) {
-    e = cudaStreamSynchronize(s->stream);  // the caller may reuse src on return
-    if (e != cudaSuccess) return cuda_fail(s, e);
+  // validate on the device: flag word ctl[3]
+  uint32_t* bad = reinterpret_cast<uint32_t*>(s->b.ctl + 3);
+  if (!e) e = cudaMemsetAsync(bad, 0, 4, s->stream);
+  if (!e) {
+    uint64_t blocks = (s->N / 4 + 255) / 256;
+    if (blocks > 152ull * 8) blocks = 152ull * 8;
+    if (blocks == 0) blocks = 1;
+    k_check_spins<<<(unsigned)blocks, 256, 0, s->stream>>>(s->b.spin, s->N, s->q, bad);
+    e = cudaGetLastError();
   }
+  uint32_t hbad = 0;
+  if (!e) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s->stream);
+  if (!e) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
   s->pending = true;
   s->measured_from = s->sweep;
+  if (hbad) {
+    s->spins_invalid = true;
+    return SW_ERR_INVAL;
+  }
+  s->spins_invalid = false;
+  return SW_OK;
+}
+
+int sw_profile(sw_sim* s, int enable) {
+  if (!s) return SW_ERR_INVAL;
+  if (enable) {
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e);
+    for (cudaEvent_t ev : s->ev_used) s->ev_pool.push_back(ev);
+    s->ev_used.clear();
+    for (int k = 0; k < 3; ++k) {
+      s->prof_ms[k] = 0;
+      s->prof_launches[k] = 0;
+    }
+  }
+  s->profiling = enable != 0;
+  return SW_OK;
+}
+
+int sw_profile_read(sw_sim* s, double* ms, uint64_t* launches, int nphase) {
+  if (!s || nphase < 0 || nphase > 3) return SW_ERR_INVAL;
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  int rc = drain_events(s);
+  if (rc) return fail(s, rc);
+  for (int k = 0; k < nphase; ++k) {
+    if (ms) ms[k] = s->prof_ms[k];
+    if (launches) launches[k] = s->prof_launches[k];
+  }
   return SW_OK;
 }
 

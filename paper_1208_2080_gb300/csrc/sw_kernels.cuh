@@ -695,6 +695,8 @@ __global__ void k_init_spins(uint8_t* s, uint64_t N, uint32_t q, uint64_t seed) 
 }
 
 // E_sat and n[s] of a configuration (the configuration no later sweep reads).
+// One thread per group of 4 sites of a row; 4-byte loads when rows are
+// 4-byte aligned, per-state counts in registers for q <= 8.
 __global__ void __launch_bounds__(256) k_measure(const uint8_t* s, Lattice lat, uint32_t q,
                                                  unsigned long long* acc) {
   __shared__ uint32_t hist[257];
@@ -703,23 +705,77 @@ __global__ void __launch_bounds__(256) k_measure(const uint8_t* s, Lattice lat, 
   const uint64_t L = lat.L;
   const uint64_t groups = (L + 3) >> 2;
   const uint64_t total = groups * L;
-  uint32_t e = 0;
+  const uint32_t qs = q <= 8 ? q - 1 : 0;
+  uint32_t e = 0, cnt[7] = {0, 0, 0, 0, 0, 0, 0}, nsites = 0;
   for (uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
        it += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t y = it / groups, x = (it % groups) * 4;
     const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
-    for (int k = 0; k < 4 && x + k < L; ++k) {
-      const uint64_t xk = x + k, xr = (xk + 1 == L) ? 0 : xk + 1;
-      const uint32_t v = s[y * L + xk];
-      e += (v == s[y * L + xr]) + (v == s[yd * L + xk]);
-      atomicAdd(&hist[1 + v], 1u);
+    uint32_t v, vr, vd, vm;
+    if (lat.vec4) {
+      v = *reinterpret_cast<const uint32_t*>(s + y * L + x);
+      const uint64_t xn = (x + 4 == L) ? 0 : x + 4;
+      const uint32_t vn = *reinterpret_cast<const uint32_t*>(s + y * L + xn);
+      vr = __funnelshift_r(v, vn, 8);
+      vd = *reinterpret_cast<const uint32_t*>(s + yd * L + x);
+      vm = 0xFFFFFFFFu;
+    } else {
+      v = vr = vd = vm = 0;
+      for (int k = 0; k < 4 && x + k < L; ++k) {
+        const uint64_t xk = x + k, xr = (xk + 1 == L) ? 0 : xk + 1;
+        v |= (uint32_t)s[y * L + xk] << (8 * k);
+        vr |= (uint32_t)s[y * L + xr] << (8 * k);
+        vd |= (uint32_t)s[yd * L + xk] << (8 * k);
+        vm |= 0xFFu << (8 * k);
+      }
+    }
+    e += __popc(__vcmpeq4(v, vr) & vm & 0x01010101u) + __popc(__vcmpeq4(v, vd) & vm & 0x01010101u);
+    nsites += __popc(vm & 0x01010101u);
+    if (qs) {
+#pragma unroll
+      for (uint32_t st = 0; st < 7; ++st)
+        if (st < qs) cnt[st] += __popc(__vcmpeq4(v, st * 0x01010101u) & vm & 0x01010101u);
+    } else {
+      for (int k = 0; k < 4; ++k)
+        if ((vm >> (8 * k)) & 1u) atomicAdd(&hist[1 + ((v >> (8 * k)) & 0xFFu)], 1u);
     }
   }
-  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(&hist[0], e);
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
+    nsites += __shfl_xor_sync(0xFFFFFFFFu, nsites, o);
+  }
+  if (qs) {
+#pragma unroll
+    for (uint32_t st = 0; st < 7; ++st)
+      for (int o = 16; o > 0; o >>= 1) cnt[st] += __shfl_xor_sync(0xFFFFFFFFu, cnt[st], o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&hist[0], e);
+    if (qs) {
+      uint32_t rest = nsites;
+      for (uint32_t st = 0; st < qs; ++st) {
+        atomicAdd(&hist[1 + st], cnt[st]);
+        rest -= cnt[st];
+      }
+      atomicAdd(&hist[1 + qs], rest);
+    }
+  }
   __syncthreads();
   for (uint32_t k = threadIdx.x; k <= q; k += blockDim.x)
     if (hist[k]) atomicAdd(&acc[k], (unsigned long long)hist[k]);
+}
+
+// Sets *bad if any of the N spins is >= q (validation of a new configuration).
+__global__ void k_check_spins(const uint8_t* s, uint64_t N, uint32_t q, uint32_t* bad) {
+  uint32_t any = 0;
+  const uint64_t nw = N >> 2;
+  const uint32_t lim = q * 0x01010101u;  // q <= 255: per-byte "value >= q" via __vcmpgeu4
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    any |= __vcmpgeu4(reinterpret_cast<const uint32_t*>(s)[i], lim);
+  if (blockIdx.x == 0)
+    for (uint64_t i = (nw << 2) + threadIdx.x; i < N; i += blockDim.x) any |= (s[i] >= q);
+  if (__any_sync(0xFFFFFFFFu, any != 0) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
 }
 
 // Files the accumulated observables as configuration ctl[0].

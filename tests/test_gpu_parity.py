@@ -205,3 +205,46 @@ def test_repeatable():
             s.sweep(10)
             out.append(s.spins())
     assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
+def test_set_spins_rejects_bad_values_on_device():
+    torch = _torch()
+    L, q = 64, 3
+    with sw.Sim(L, q, sw.tc(q), 9) as s:
+        bad = torch.full((L * L,), 3, dtype=torch.uint8, device="cuda")
+        with pytest.raises(sw.SwError) as e:
+            s.set_spins(bad)
+        assert e.value.code == sw._binding.SW_ERR_INVAL
+        with pytest.raises(sw.SwError) as e:
+            s.sweep(1)
+        assert e.value.code == sw._binding.SW_ERR_STATE
+        s.set_spins(np.zeros((L, L), np.uint8))
+        s.sweep(1)
+        ref, _, _ = oracle.run(L, q, sw.tc(q), 9, 1, spins=np.zeros((L, L), np.uint8))
+        assert np.array_equal(s.spins(), ref)
+
+
+def test_profile_counts_launches():
+    L, q = 300, 2
+    with sw.Sim(L, q, sw.tc(q), 1) as s:
+        s.profile(True)
+        s.sweep(5)
+        ms, n = s.profile_read()
+        assert n == [5, 5, 5] and all(m > 0 for m in ms)
+        s.profile(False)
+        s.sweep(2)
+        assert s.profile_read()[1] == [5, 5, 5]
+
+
+def test_large_lattice_properties():
+    """L = 8192 (67M sites): a few sweeps bit-exact against the oracle for
+    q = 2, 3, 4 at T_c, random start."""
+    L, n = 8192, 2
+    for q in (2, 3, 4):
+        with sw.Sim(L, q, sw.tc(q), 2 + q) as s:
+            s.sweep(n)
+            got = s.spins()
+            E, nn = s.series(1, n)
+        ref, refE, refn = oracle.run(L, q, sw.tc(q), 2 + q, n)
+        assert np.array_equal(E, refE) and np.array_equal(nn, refn)
+        assert np.array_equal(got, ref)
