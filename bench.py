@@ -39,8 +39,9 @@ PAPER_UPDATE_MEASURE = 33.85  # Table 1, L=65536, 256x Tesla M2050, update + mea
 # design: k_label_tile reads the uint8 spin and writes the 16-bit site code;
 # k_recolor reads the code and writes the spin.  O(1/tile) halo and edge
 # terms are left out.
-ALG_BYTES_PER_SITE = {"k_label_tile": 3.0, "k_merge": 0.0, "k_recolor": 3.0}
-PHASES = ["k_label_tile", "k_merge", "k_recolor"]
+ALG_BYTES_PER_SITE = {"k_label_tile": 3.0, "k_merge+k_resolve": 0.0, "k_recolor": 3.0}
+PHASES = ["k_label_tile", "k_merge+k_resolve", "k_recolor"]
+LAUNCHES_PER_SWEEP = 4  # k_label_tile, k_merge, k_resolve, k_recolor
 THROTTLE = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
 
@@ -200,7 +201,7 @@ def run_ours(args, rank, world):
     N = L * L
     T = sw.tc(q)
     seed = 5 + rank
-    sim = sw.Sim(L, q, T, seed, init="zero", label_bits=args.label_bits)
+    sim = sw.Sim(L, q, T, seed, init="zero", label_bits=args.label_bits, tile_h=args.tile_h)
     info = sim.info()
     stream = torch.cuda.current_stream()
     sim.sweep(args.warmup)
@@ -240,7 +241,8 @@ def run_ours(args, rank, world):
         sim.close()
         sim = None
         torch.cuda.empty_cache()
-        sim2 = sw.Sim(L, q, T, seed, measure=False, label_bits=args.label_bits)
+        sim2 = sw.Sim(L, q, T, seed, measure=False, label_bits=args.label_bits,
+                      tile_h=args.tile_h)
         sim2.set_spins(spins_dev)
         sim2.set_sweep(cur)
         del spins_dev
@@ -301,7 +303,7 @@ def run_ours(args, rank, world):
                    "L": L, "q": q, "tile": f"{info['tile_w']}x{info['tile_h']}",
                    "l2": "inputs larger than L2 (4 GiB spins, 8 GiB codes at L=65536)",
                    "replicas": world},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": LAUNCHES_PER_SWEEP * args.steps,
         "roofline": roof,
         "clocks": clk.summary(),
         "e2e": e2e,
@@ -325,6 +327,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--L", type=int, default=65536, help="lattice size (default: the workload)")
     ap.add_argument("--label-bits", type=int, default=0, help="0 = auto (64 above L=32768)")
+    ap.add_argument("--tile-h", type=int, default=0, help="labelling tile height (0 = auto)")
     ap.add_argument("--ref-L", type=int, default=4096, help="oracle sample size per reference step")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--update-only-steps", type=int, default=20)

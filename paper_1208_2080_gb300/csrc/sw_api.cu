@@ -85,9 +85,24 @@ static cudaError_t launch_label_t(const Bufs& b, const Lattice& lat, cudaStream_
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     configured = true;
   }
-  kern<<<lat.ntiles, kThreads, smem, st>>>(b, lat);
+  // persistent grid: as many tile CTAs as fit on the GPU at once
+  static int resident = 0;
+  if (!resident) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TileCta<TH>::kThreads, smem);
+    if (sms <= 0) sms = 152;
+    if (per_sm <= 0) per_sm = 1;
+    resident = sms * per_sm;
+  }
+  const uint32_t grid = lat.ntiles < (uint32_t)resident ? lat.ntiles : (uint32_t)resident;
+  kern<<<grid, TileCta<TH>::kThreads, smem, st>>>(b, lat);
   return cudaGetLastError();
 }
 
@@ -96,6 +111,14 @@ static cudaError_t launch_merge_t(const Bufs& b, const Lattice& lat, cudaStream_
   const uint64_t items = (uint64_t)lat.ntiles * (TH + kTW);
   const uint64_t blocks = (items + kMergeThreads - 1) / kMergeThreads;
   k_merge<TH, LabelT><<<(unsigned)blocks, kMergeThreads, 0, st>>>(b, lat);
+  return cudaGetLastError();
+}
+
+template <int TH, typename LabelT>
+static cudaError_t launch_resolve_t(const Bufs& b, const Lattice& lat, cudaStream_t st) {
+  const uint64_t items = (uint64_t)lat.ntiles * TileRec<TH>::kOpenCap;
+  const uint64_t blocks = (items + kMergeThreads - 1) / kMergeThreads;
+  k_resolve<TH, LabelT><<<(unsigned)blocks, kMergeThreads, 0, st>>>(b, lat);
   return cudaGetLastError();
 }
 
@@ -113,6 +136,7 @@ static cudaError_t sweep_once_t(uint32_t th, const Bufs& b, const Lattice& lat, 
   case THV:                                                                   \
     if ((e = launch_label_t<THV, LabelT, false, false>(b, lat, st))) return e; \
     if ((e = launch_merge_t<THV, LabelT>(b, lat, st))) return e;              \
+    if ((e = launch_resolve_t<THV, LabelT>(b, lat, st))) return e;            \
     return launch_recolor_t<THV, LabelT, false>(b, lat, nullptr, st);
     SWGB_CASE(16)
     SWGB_CASE(32)
@@ -136,6 +160,7 @@ static cudaError_t sweep_once_ev_t(uint32_t th, const Bufs& b, const Lattice& la
     if ((e = launch_label_t<THV, LabelT, false, false>(b, lat, st))) return e; \
     if ((e = cudaEventRecord(ev[1], st))) return e;                           \
     if ((e = launch_merge_t<THV, LabelT>(b, lat, st))) return e;              \
+    if ((e = launch_resolve_t<THV, LabelT>(b, lat, st))) return e;            \
     if ((e = cudaEventRecord(ev[2], st))) return e;                           \
     if ((e = launch_recolor_t<THV, LabelT, false>(b, lat, nullptr, st))) return e; \
     return cudaEventRecord(ev[3], st);
@@ -385,12 +410,13 @@ int sw_create_ex(const sw_params* prm, sw_sim** out) {
   b.ebits = (uint32_t*)take(s, nt * bit_words(th) * 4);
   b.olist = (uint16_t*)take(s, nt * open_cap(th) * 2);
   b.ocnt = (uint32_t*)take(s, nt * 4);
+  b.nso = (uint8_t*)take(s, nt * open_cap(th));
   b.acc = (unsigned long long*)take(s, 8 * 260);
   b.ring = (unsigned long long*)take(s, (size_t)ring * (2 + s->q) * 8);
   b.ctl = (unsigned long long*)take(s, 64);
   b.err = (uint32_t*)take(s, 64);
   if (!b.spin || !b.code || (prm->store_bonds && !b.bonds) || !b.T || !b.edge || !b.ebits ||
-      !b.olist || !b.ocnt || !b.acc || !b.ring || !b.ctl || !b.err) {
+      !b.olist || !b.ocnt || !b.nso || !b.acc || !b.ring || !b.ctl || !b.err) {
     release_all(s);
     delete s;
     return SW_ERR_NOMEM;

@@ -66,16 +66,29 @@ struct TileRec {
   static constexpr int kOpenCap = 2 * TH + 2 * kTW;        // open roots <= edge sites
 };
 
+// Tile CTA shape: a warp owns 4 consecutive rows, so a 128 x TH tile is
+// labelled by TH/4 warps.
+template <int TH>
+struct TileCta {
+  static constexpr int kRpw = 4;                 // rows per warp
+  static constexpr int kWarps = TH / kRpw;       // warps per CTA
+  static constexpr int kThreads = 32 * kWarps;
+  static constexpr int kMinBlocks = 128 / TH;    // keeps the register budget at 64
+};
+
 // Shared-memory layout of k_label_tile.
 template <int TH>
 struct LabelSmem {
+  static constexpr int kNW = TileCta<TH>::kWarps;
   static constexpr int kP = 0;                                     // u32 [kTW*TH] union-find
-  static constexpr int kSp = kP + 4 * kTW * TH;                    // u8 [(TH+1)*kSpPitch]
-  static constexpr int kRbn = align16(kSp + (TH + 1) * kSpPitch);  // u8 [TH*32] right-bond nibbles
-  static constexpr int kCb = align16(kRbn + TH * 32);              // u32 cross bits
-  static constexpr int kCnt = align16(kCb + 4 * TileRec<TH>::kBitWords);  // u32 [4]
-  static constexpr int kObs = align16(kCnt + 16);                  // u32 [1 + 256]
-  static constexpr int kCl = align16(kObs + 4 * 257);              // u16 [kTW*TH] closed roots
+  static constexpr int kSpBuf = align16((TH + 1) * kSpPitch);      // one staged tile of spins
+  static constexpr int kSp = kP + 4 * kTW * TH;                    // u8 [2][kSpBuf] double buffer
+  static constexpr int kRbn = kSp + 2 * kSpBuf;                    // u8 [TH*32] right-bond nibbles
+  static constexpr int kQ = align16(kRbn + TH * 32);               // u16 [kNW*kTW] task queues
+  static constexpr int kCb = align16(kQ + 2 * kNW * kTW);          // u32 cross bits
+  static constexpr int kCnt = align16(kCb + 4 * TileRec<TH>::kBitWords);  // u32 [kNW]
+  static constexpr int kObs = align16(kCnt + 4 * kNW);             // u32 [1 + 256]
+  static constexpr int kCl = align16(kObs + 4 * 257);              // u16 [kTW*TH] root lists
   static constexpr int kBytes = align16(kCl + 2 * kTW * TH);
 };
 
@@ -96,6 +109,7 @@ struct Bufs {
   uint32_t* ebits;            // ntiles * kBitWords
   uint16_t* olist;            // ntiles * kOpenCap
   uint32_t* ocnt;             // ntiles
+  uint8_t* nso;               // ntiles * kOpenCap: new state of each open root
   unsigned long long* acc;    // [1 + q]: E_sat, n[q] of the configuration being measured
   unsigned long long* ring;   // [ring_cap][2 + q]: tag, E_sat, n[q]
   unsigned long long* ctl;    // [0] next sweep, [1] sweep being recoloured
@@ -117,7 +131,28 @@ __device__ __forceinline__ void tile_geom(const Lattice& lat, uint32_t t, int TH
 }
 
 // ---------------------------------------------------------------- shared-memory union-find
-__device__ __forceinline__ uint32_t find_local(const uint32_t* P, uint32_t x, uint32_t& bad) {
+// Entries are tile-local site indices and every parent is <= its child, so a
+// walk strictly decreases and ends at a root (bounded anyway).  Path halving
+// stores only replace a parent by one of its ancestors, which cannot undo a
+// concurrent atomicMin link (the union retries with the old parent).
+__device__ __forceinline__ uint32_t find_local(uint32_t* P, uint32_t x, uint32_t& bad) {
+  volatile uint32_t* vp = P;
+  for (uint32_t it = 0; it < kLocalCap; ++it) {
+    const uint32_t p = vp[x];
+    if (p == x) return x;
+    const uint32_t gp = vp[p];
+    if (gp == p) return p;
+    vp[x] = gp;
+    x = gp;
+  }
+  bad = 1;
+  return x;
+}
+
+// Read-only walk, for the compression pass: there, every run start must end
+// up pointing straight at its root, which halving stores by other threads
+// could undo.
+__device__ __forceinline__ uint32_t root_local(const uint32_t* P, uint32_t x, uint32_t& bad) {
   const volatile uint32_t* vp = P;
   for (uint32_t it = 0; it < kLocalCap; ++it) {
     const uint32_t p = vp[x];
@@ -143,6 +178,67 @@ __device__ __forceinline__ void unite_local(uint32_t* P, uint32_t a, uint32_t b,
     a = old;  // a was no longer a root: join its new parent instead
   }
   bad = 1;
+}
+
+// Root of x once all unions are done (roots may carry flag bits above
+// kIdx); returns the root and its raw entry.  Halving stores touch only
+// non-root entries, which carry no flags.
+__device__ __forceinline__ uint32_t walk_root(uint32_t* P, uint32_t x, uint32_t& vroot, uint32_t& bad) {
+  volatile uint32_t* vp = P;
+  for (uint32_t it = 0; it < kLocalCap; ++it) {
+    const uint32_t v = vp[x];
+    const uint32_t p = v & kIdx;
+    if (p == x) {
+      vroot = v;
+      return x;
+    }
+    const uint32_t v2 = vp[p];
+    const uint32_t gp = v2 & kIdx;
+    if (gp == p) {
+      vroot = v2;
+      return p;
+    }
+    vp[x] = gp;
+    x = gp;
+  }
+  bad = 1;
+  vroot = 0;
+  return x;
+}
+
+// Read-only walk to the root, ignoring flag bits above kIdx (used while
+// other threads compress starts and flag roots).
+__device__ __forceinline__ uint32_t root_masked(const uint32_t* P, uint32_t x, uint32_t& bad) {
+  const volatile uint32_t* vp = P;
+  for (uint32_t it = 0; it < kLocalCap; ++it) {
+    const uint32_t p = vp[x] & kIdx;
+    if (p == x) return x;
+    x = p;
+  }
+  bad = 1;
+  return x;
+}
+
+// Warp-level compaction: lane l contributes the sites (4l+k, k in `mask`)
+// of row base `rowbase`; returns the number of tasks written to q[0..n).
+__device__ __forceinline__ uint32_t warp_enqueue(uint16_t* q, uint32_t mask, uint32_t rowbase,
+                                                 int lane) {
+  const uint32_t mine = (uint32_t)__popc(mask);
+  uint32_t inc = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  uint32_t pos = inc - mine;
+  while (mask) {
+    const int k = __ffs(mask) - 1;
+    mask &= mask - 1u;
+    q[pos++] = (uint16_t)(rowbase + 4 * lane + k);
+  }
+  const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+  __syncwarp();
+  return total;
 }
 
 // ---------------------------------------------------------------- global union-find
@@ -201,6 +297,14 @@ __device__ __forceinline__ uint64_t global_index(const Lattice& lat, uint64_t x0
   return (y0 + (local >> 7)) * lat.L + x0 + (local & (kTW - 1));
 }
 
+// 4-byte asynchronous global -> shared copy (completes at cp_async_wait).
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t byte_mask(uint32_t nib) {
   // 4-bit site mask -> 0xFF per selected byte
   return ((nib & 1u) ? 0x000000FFu : 0u) | ((nib & 2u) ? 0x0000FF00u : 0u) |
@@ -208,321 +312,440 @@ __device__ __forceinline__ uint32_t byte_mask(uint32_t nib) {
 }
 
 // ================================================================== k_label_tile
+// Persistent: CTA c labels tiles c, c + gridDim.x, ...; while it works on one
+// tile the next tile's spin rows are already in flight into registers.
+//
 // kGiven: bonds are read from b.bonds instead of drawn (labelling-only entry).
 // kRoots: closed clusters keep their local root in the code (no new state).
+//
+// Union-find entries P[j] hold tile-local site indices j = ly*128 + lx
+// (15 bits).  A site that is not the start of its horizontal run keeps
+// pointing at its run start for the whole tile; only run starts take part
+// in unions, so only they are compressed, and every site's root is
+// P[P[j] & kIdx] & kIdx.  Once the root lists are built, a root entry also
+// carries kOpen and, in bits 16..24, its open-root slot (open) or its new
+// state (closed).  Lane l owns sites 4l..4l+3 of a row; its four entries are
+// moved with one 16-byte shared-memory access (conflict free); unions and
+// compressions are compacted into per-warp task queues so that all lanes
+// stay busy.
 template <int TH, typename LabelT, bool kGiven, bool kRoots>
-__global__ void __launch_bounds__(kThreads) k_label_tile(const Bufs b, const Lattice lat) {
-  static_assert(TH % kWarps == 0 && kTW * TH <= 32768, "tile shape");
+__global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks)
+    k_label_tile(const Bufs b, const Lattice lat) {
+  static_assert(TH % 16 == 0 && kTW * TH <= 32768, "tile shape");
   using S = LabelSmem<TH>;
   using R = TileRec<TH>;
-  constexpr int kRpw = TH / kWarps;  // rows per warp
+  constexpr int kRpw = TileCta<TH>::kRpw;       // rows per warp
+  constexpr int kWarps = TileCta<TH>::kWarps;    // shadows the recolour CTA shape
+  constexpr int kThreads = TileCta<TH>::kThreads;
   constexpr unsigned kFull = 0xFFFFFFFFu;
 
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* P = reinterpret_cast<uint32_t*>(smem + S::kP);
   uint8_t* sp = smem + S::kSp;
   uint8_t* rbn = smem + S::kRbn;
+  uint16_t* wq = reinterpret_cast<uint16_t*>(smem + S::kQ);
   uint32_t* cbits = reinterpret_cast<uint32_t*>(smem + S::kCb);
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + S::kCnt);
+  uint32_t* wcnt = reinterpret_cast<uint32_t*>(smem + S::kCnt);
   uint32_t* sobs = reinterpret_cast<uint32_t*>(smem + S::kObs);
   uint16_t* clist = reinterpret_cast<uint16_t*>(smem + S::kCl);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t t = blockIdx.x;
-  uint64_t x0, y0;
-  int w, h;
-  tile_geom(lat, t, TH, x0, y0, w, h);
+  const int lx0 = 4 * lane;
+  uint16_t* q = wq + warp * kTW;
   const uint64_t L = lat.L;
-  const uint32_t q = b.q;
+  const uint32_t q_states = b.q;
   const bool measure = !kGiven && b.measure;
   const uint32_t sweep = kGiven ? 0u : (uint32_t)b.ctl[0];
   uint32_t bad = 0;
+  LabelT* T = reinterpret_cast<LabelT*>(b.T);
 
-  for (int k = tid; k < R::kBitWords; k += kThreads) cbits[k] = 0;
-  if (tid < 4) cnt[tid] = 0;
   if (measure)
     for (int k = tid; k < 257; k += kThreads) sobs[k] = 0;
+  uint32_t e_loc = 0, nsites = 0;
+  uint32_t ncnt[3] = {0, 0, 0};
+  const uint32_t qs = q_states <= 4 ? q_states - 1 : 0;  // states counted in registers
 
-  // ---- stage spins (tile rows 0..h-1 plus the halo row h and column w)
-  if (!kGiven) {
-    for (int ly = warp; ly <= h; ly += kWarps) {
-      const uint64_t gy = (ly < h) ? (y0 + ly) : ((y0 + h) % L);
-      const uint8_t* row = b.spin + gy * L + x0;
-      uint32_t v = 0;
-      const int lx0 = 4 * lane;
-      if (lx0 < w) {
-        if (lat.vec4) {
-          v = *reinterpret_cast<const uint32_t*>(row + lx0);
-        } else {
+  // ---- stage a tile's spin rows (0..h-1 and the halo row h) plus each
+  // row's halo byte at column w into a shared buffer.  Rows start 4-byte
+  // aligned when L % 4 == 0: then the copies are asynchronous (cp.async)
+  // and the next tile is staged while this one is labelled.
+  auto stage = [&](uint32_t tt, uint8_t* buf, bool async) {
+    uint64_t fx0, fy0;
+    int fw, fh;
+    tile_geom(lat, tt, TH, fx0, fy0, fw, fh);
+    for (int ly = warp; ly <= fh; ly += kWarps) {
+      const uint64_t gy = (ly < fh) ? (fy0 + ly) : ((fy0 + fh) % L);
+      const uint8_t* row = b.spin + gy * L + fx0;
+      uint8_t* dst = buf + ly * kSpPitch;
+      if (async) {
+        if (lx0 < fw) cp_async4(dst + lx0, row + lx0);
+        // halo column: 4 aligned bytes starting at column (x0 + w) mod L
+        if (lane == 31) cp_async4(dst + fw, b.spin + gy * L + (fx0 + fw) % L);
+      } else {
+        uint32_t v = 0;
+        if (lx0 < fw) {
 #pragma unroll
           for (int k = 0; k < 4; ++k)
-            if (lx0 + k < w) v |= (uint32_t)row[lx0 + k] << (8 * k);
+            if (lx0 + k < fw) v |= (uint32_t)row[lx0 + k] << (8 * k);
         }
+        *reinterpret_cast<uint32_t*>(dst + lx0) = v;
+        __syncwarp();
+        if (lane == 0) dst[fw] = b.spin[gy * L + (fx0 + fw) % L];
       }
-      *reinterpret_cast<uint32_t*>(sp + ly * kSpPitch + lx0) = v;
-      __syncwarp();
-      if (lane == 0) sp[ly * kSpPitch + w] = b.spin[gy * L + (x0 + w) % L];
     }
+  };
+  const bool async_stage = !kGiven && lat.vec4;
+  if (async_stage && blockIdx.x < lat.ntiles) {
+    stage(blockIdx.x, sp, true);
+    cp_async_commit();
   }
-  __syncthreads();
 
-  // ---- bonds, measurement, horizontal runs
-  const int lx0 = 4 * lane;
-  uint32_t R4[kRpw], D4[kRpw];
-  uint32_t e_loc = 0;
-  uint32_t ncnt[7] = {0, 0, 0, 0, 0, 0, 0};
-  const uint32_t qs = q <= 8 ? q - 1 : 0;  // states counted in registers
-#pragma unroll
-  for (int rr = 0; rr < kRpw; ++rr) {
-    const int ly = warp + rr * kWarps;
-    uint32_t vm = 0;  // valid sites of this lane's group
-    if (ly < h) {
-      const int nv = w - lx0;
-      vm = nv >= 4 ? 0xFu : (nv > 0 ? (1u << nv) - 1u : 0u);
+  uint32_t it = 0;
+  for (uint32_t t = blockIdx.x; t < lat.ntiles; t += gridDim.x, ++it) {
+    uint64_t x0, y0;
+    int w, h;
+    tile_geom(lat, t, TH, x0, y0, w, h);
+    uint8_t* spc = sp + (it & 1u) * S::kSpBuf;  // this tile's staged spins
+    if (tid < R::kBitWords) cbits[tid] = 0;
+    if (async_stage) {
+      cp_async_wait();
+      __syncthreads();  // every thread's copies of this tile have landed
+      if (t + gridDim.x < lat.ntiles) {
+        stage(t + gridDim.x, sp + ((it + 1) & 1u) * S::kSpBuf, true);
+        cp_async_commit();
+      }
+    } else if (!kGiven) {
+      stage(t, spc, false);
     }
-    uint32_t br = 0, bd = 0;  // active bonds (right / down), all of them
-    if (kGiven) {
-      if (vm) {
-        const uint32_t byte = b.bonds[(y0 + ly) * lat.bp + ((x0 + lx0) >> 2)];
+    if (tid == 0) nsites += (uint32_t)(w * h);
+    __syncthreads();
+
+    // ---- bonds, measurement, horizontal runs
+    uint32_t rowbits[kRpw];  // bits 0-3 internal right, 4-7 internal down, 8-11 run starts
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          br |= ((byte >> (2 * k)) & 1u) << k;
-          bd |= ((byte >> (2 * k + 1)) & 1u) << k;
+    for (int rr = 0; rr < kRpw; ++rr) {
+      const int ly = warp * kRpw + rr;  // a warp owns a block of kRpw consecutive rows
+      uint32_t vm = 0;  // valid sites of this lane's group
+      if (ly < h) {
+        const int nv = w - lx0;
+        vm = nv >= 4 ? 0xFu : (nv > 0 ? (1u << nv) - 1u : 0u);
+      }
+      uint32_t br = 0, bd = 0;  // active bonds (right / down), all of them
+      if (kGiven) {
+        if (vm) {
+          const uint32_t byte = b.bonds[(y0 + ly) * lat.bp + ((x0 + lx0) >> 2)];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            br |= ((byte >> (2 * k)) & 1u) << k;
+            bd |= ((byte >> (2 * k + 1)) & 1u) << k;
+          }
+          br &= vm;
+          bd &= vm;
         }
-        br &= vm;
-        bd &= vm;
-      }
-    } else {
-      const uint32_t s = *reinterpret_cast<const uint32_t*>(sp + ly * kSpPitch + lx0);
-      const uint32_t sn = *reinterpret_cast<const uint32_t*>(sp + ly * kSpPitch + lx0 + 4);
-      const uint32_t sd = *reinterpret_cast<const uint32_t*>(sp + (ly + 1) * kSpPitch + lx0);
-      const uint32_t sr = __funnelshift_r(s, sn, 8);
-      const uint32_t vb = byte_mask(vm);
-      const uint32_t eqr = __vcmpeq4(s, sr) & vb;
-      const uint32_t eqd = __vcmpeq4(s, sd) & vb;
-      if (measure) {
-        e_loc += __popc(eqr & 0x01010101u) + __popc(eqd & 0x01010101u);
-        if (qs) {
+      } else {
+        const uint32_t s = *reinterpret_cast<const uint32_t*>(spc + ly * kSpPitch + lx0);
+        const uint32_t sn = *reinterpret_cast<const uint32_t*>(spc + ly * kSpPitch + lx0 + 4);
+        const uint32_t sd = *reinterpret_cast<const uint32_t*>(spc + (ly + 1) * kSpPitch + lx0);
+        const uint32_t sr = __funnelshift_r(s, sn, 8);
+        const uint32_t vb = byte_mask(vm);
+        const uint32_t eqr = __vcmpeq4(s, sr) & vb;
+        const uint32_t eqd = __vcmpeq4(s, sd) & vb;
+        if (measure) {
+          e_loc += __popc(eqr & 0x01010101u) + __popc(eqd & 0x01010101u);
+          if (qs) {
 #pragma unroll
-          for (uint32_t st = 0; st < 7; ++st)
-            if (st < qs) ncnt[st] += __popc(__vcmpeq4(s, st * 0x01010101u) & vb & 0x01010101u);
-        } else {
+            for (uint32_t st = 0; st < 3; ++st)
+              if (st < qs) ncnt[st] += __popc(__vcmpeq4(s, st * 0x01010101u) & vb & 0x01010101u);
+          } else {
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (vm & (1u << k)) atomicAdd(&sobs[1 + ((s >> (8 * k)) & 0xFFu)], 1u);
+            for (int k = 0; k < 4; ++k)
+              if (vm & (1u << k)) atomicAdd(&sobs[1 + ((s >> (8 * k)) & 0xFFu)], 1u);
+          }
+        }
+        if ((eqr | eqd) != 0u) {
+          const uint64_t i0 = (y0 + ly) * L + x0 + lx0;
+          const uint64_t pa = i0 >> 1;
+          const Words4 A = stream4(b.seed, pa, sweep, kDomBond);
+          const Words4 B = stream4(b.seed, pa + 1, sweep, kDomBond);
+          uint32_t wr[4], wd[4];
+          if ((i0 & 1u) == 0u) {
+            wr[0] = A.x; wd[0] = A.y; wr[1] = A.z; wd[1] = A.w;
+            wr[2] = B.x; wd[2] = B.y; wr[3] = B.z; wd[3] = B.w;
+          } else {
+            const Words4 C = stream4(b.seed, pa + 2, sweep, kDomBond);
+            wr[0] = A.z; wd[0] = A.w; wr[1] = B.x; wd[1] = B.y;
+            wr[2] = B.z; wd[2] = B.w; wr[3] = C.x; wd[3] = C.y;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            br |= (((eqr >> (8 * k)) & 1u) & (wr[k] < b.thr ? 1u : 0u)) << k;
+            bd |= (((eqd >> (8 * k)) & 1u) & (wd[k] < b.thr ? 1u : 0u)) << k;
+          }
+        }
+        if (b.bonds && vm) {
+          uint32_t byte = 0;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) byte |= (((br >> k) & 1u) << (2 * k)) | (((bd >> k) & 1u) << (2 * k + 1));
+          b.bonds[(y0 + ly) * lat.bp + ((x0 + lx0) >> 2)] = (uint8_t)byte;
         }
       }
-      if ((eqr | eqd) != 0u) {
-        const uint64_t i0 = (y0 + ly) * L + x0 + lx0;
-        const uint64_t pa = i0 >> 1;
-        const Words4 A = stream4(b.seed, pa, sweep, kDomBond);
-        const Words4 B = stream4(b.seed, pa + 1, sweep, kDomBond);
-        uint32_t wr[4], wd[4];
-        if ((i0 & 1u) == 0u) {
-          wr[0] = A.x; wd[0] = A.y; wr[1] = A.z; wd[1] = A.w;
-          wr[2] = B.x; wd[2] = B.y; wr[3] = B.z; wd[3] = B.w;
-        } else {
-          const Words4 C = stream4(b.seed, pa + 2, sweep, kDomBond);
-          wr[0] = A.z; wd[0] = A.w; wr[1] = B.x; wd[1] = B.y;
-          wr[2] = B.z; wd[2] = B.w; wr[3] = C.x; wd[3] = C.y;
-        }
+      // internal vs cross-edge bonds
+      const int last = w - 1 - lx0;  // position of the tile's last column in this group
+      const uint32_t rint = (last >= 4) ? 0xFu : (last > 0 ? (1u << last) - 1u : 0u);
+      if (last >= 0 && last < 4 && ((br >> last) & 1u)) atomicOr(&cbits[ly >> 5], 1u << (ly & 31));
+      if (ly == h - 1) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          br |= (((eqr >> (8 * k)) & 1u) & (wr[k] < b.thr ? 1u : 0u)) << k;
-          bd |= (((eqd >> (8 * k)) & 1u) & (wd[k] < b.thr ? 1u : 0u)) << k;
+        for (int m = 0; m < 4; ++m) {
+          const uint32_t v = (lane >> 3) == m ? (bd & 0xFu) << (4 * (lane & 7)) : 0u;
+          const uint32_t word = __reduce_or_sync(kFull, v);
+          if (lane == 0) cbits[R::kRightWords + m] = word;
         }
       }
-      if (b.bonds && vm) {
-        uint32_t byte = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) byte |= (((br >> k) & 1u) << (2 * k)) | (((bd >> k) & 1u) << (2 * k + 1));
-        b.bonds[(y0 + ly) * lat.bp + ((x0 + lx0) >> 2)] = (uint8_t)byte;
-      }
-    }
-    // internal vs cross-edge bonds
-    const int last = w - 1 - lx0;  // position of the tile's last column in this group
-    const uint32_t rint = (last >= 4) ? 0xFu : (last > 0 ? (1u << last) - 1u : 0u);
-    if (last >= 0 && last < 4 && ((br >> last) & 1u)) atomicOr(&cbits[ly >> 5], 1u << (ly & 31));
-    if (ly == h - 1) {
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const uint32_t v = (lane >> 3) == m ? (bd & 0xFu) << (4 * (lane & 7)) : 0u;
-        const uint32_t word = __reduce_or_sync(kFull, v);
-        if (lane == 0) cbits[R::kRightWords + m] = word;
-      }
-    }
-    const uint32_t r4 = br & rint;
-    const uint32_t d4 = (ly < h - 1) ? bd : 0u;
-    R4[rr] = r4;
-    D4[rr] = d4;
-    // horizontal runs: a site whose left bond is inactive starts a run; every
-    // site's provisional label is its run start (one ballot per row)
-    uint32_t prev3 = __shfl_up_sync(kFull, (r4 >> 3) & 1u, 1);
-    if (lane == 0) prev3 = 0;
-    const uint32_t brk = (~((r4 << 1) | prev3)) & 0xFu;
-    const uint32_t B = __ballot_sync(kFull, brk != 0u);
-    const int lb = brk ? 31 - __clz(brk) : 0;
-    const uint32_t below = B & ((1u << lane) - 1u);
-    const int src = below ? 31 - __clz(below) : 0;
-    const int lbs = __shfl_sync(kFull, lb, src);
-    if (ly < TH) {
+      const uint32_t r4 = br & rint;
+      const uint32_t d4 = (ly < h - 1) ? bd : 0u;
+      // horizontal runs: a site whose left bond is inactive starts a run;
+      // every site's provisional label is its run start (one ballot per row)
+      uint32_t prev3 = __shfl_up_sync(kFull, (r4 >> 3) & 1u, 1);
+      if (lane == 0) prev3 = 0;
+      const uint32_t brk = (~((r4 << 1) | prev3)) & 0xFu;
+      rowbits[rr] = r4 | (d4 << 4) | ((brk & vm) << 8);
+      const uint32_t Bm = __ballot_sync(kFull, brk != 0u);
+      const int lb = brk ? 31 - __clz(brk) : 0;
+      const uint32_t below = Bm & ((1u << lane) - 1u);
+      const int src = below ? 31 - __clz(below) : 0;
+      const int lbs = __shfl_sync(kFull, lb, src);
+      const uint32_t rowbase = (uint32_t)(ly * kTW);
+      uint32_t st4[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const uint32_t m = brk & ((2u << k) - 1u);
-        const int start = m ? lx0 + 31 - __clz(m) : 4 * src + lbs;
-        P[ly * kTW + lx0 + k] = (uint32_t)(ly * kTW + start);
+        st4[k] = rowbase + (uint32_t)(m ? lx0 + 31 - __clz(m) : 4 * src + lbs);
       }
+      *reinterpret_cast<uint4*>(P + rowbase + lx0) = make_uint4(st4[0], st4[1], st4[2], st4[3]);
       rbn[ly * 32 + lane] = (uint8_t)r4;
     }
-  }
-  __syncthreads();
+    __syncthreads();
 
-  // ---- vertical unions (skip the ones that repeat the left neighbour's)
-#pragma unroll
-  for (int rr = 0; rr < kRpw; ++rr) {
-    const int ly = warp + rr * kWarps;
-    if (ly < h - 1) {
-      const uint32_t d4 = D4[rr], r4 = R4[rr];
-      const uint32_t rb = rbn[(ly + 1) * 32 + lane];
+    // ---- vertical unions.  Each warp first links its own rows top-down,
+    // one row pair at a time, so a new run is hung directly under an
+    // existing root and trees stay shallow; then the kWarps-1 row pairs that
+    // straddle two warps' blocks are linked.  Unions that repeat the left
+    // neighbour's union of the same two runs are skipped, the rest are
+    // compacted into the warp's task queue so all lanes stay busy.
+    auto link_rows = [&](int ly, uint32_t r4, uint32_t d4, uint32_t rb, uint32_t pb) {
       uint32_t pd = __shfl_up_sync(kFull, (d4 >> 3) & 1u, 1);
       uint32_t pr = __shfl_up_sync(kFull, (r4 >> 3) & 1u, 1);
-      uint32_t pb = lane > 0 ? (rbn[(ly + 1) * 32 + lane - 1] >> 3) & 1u : 0u;
       if (lane == 0) pd = pr = pb = 0;
       const uint32_t skip = ((d4 << 1) | pd) & ((r4 << 1) | pr) & ((rb << 1) | pb);
-      uint32_t todo = d4 & ~skip & 0xFu;
-      while (todo) {
-        const int k = __ffs(todo) - 1;
-        todo &= todo - 1u;
-        const uint32_t a = (uint32_t)(ly * kTW + lx0 + k);
-        unite_local(P, a, a + kTW, bad);
+      const uint32_t n = warp_enqueue(q, d4 & ~skip & 0xFu, (uint32_t)(ly * kTW), lane);
+      for (uint32_t i = lane; i < n; i += 32) {
+        const uint32_t a = q[i];
+        unite_local(P, P[a], P[a + kTW], bad);
+      }
+      __syncwarp();
+    };
+#pragma unroll
+    for (int rr = 0; rr + 1 < kRpw; ++rr) {
+      const int ly = warp * kRpw + rr;
+      if (ly < h - 1) {  // warp-uniform
+        const uint32_t rb = rowbits[rr + 1] & 0xFu;
+        const uint32_t pb = __shfl_up_sync(kFull, (rb >> 3) & 1u, 1);
+        link_rows(ly, rowbits[rr] & 0xFu, (rowbits[rr] >> 4) & 0xFu, rb, pb);
       }
     }
-  }
-  __syncthreads();
-
-  // ---- compress: every site points at its tile-local root
-#pragma unroll
-  for (int rr = 0; rr < kRpw; ++rr) {
-    const int ly = warp + rr * kWarps;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint32_t j = (uint32_t)(ly * kTW + lx0 + k);
-      P[j] = find_local(P, j, bad);
-    }
-  }
-  __syncthreads();
-
-  // ---- mark clusters that touch the tile edge as open
-#pragma unroll
-  for (int rr = 0; rr < kRpw; ++rr) {
-    const int ly = warp + rr * kWarps;
-    if (ly < h) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int lx = lx0 + k;
-        if (lx < w && (lx == 0 || lx == w - 1 || ly == 0 || ly == h - 1)) {
-          const uint32_t j = (uint32_t)(ly * kTW + lx);
-          atomicOr(&P[P[j] & kIdx], kOpen);
-        }
+    __syncthreads();
+    {
+      const int ly = warp * kRpw + kRpw - 1;
+      if (warp + 1 < kWarps && ly < h - 1) {  // warp-uniform
+        const uint32_t rb = rbn[(ly + 1) * 32 + lane];
+        const uint32_t pb = lane > 0 ? (rbn[(ly + 1) * 32 + lane - 1] >> 3) & 1u : 0u;
+        link_rows(ly, rowbits[kRpw - 1] & 0xFu, (rowbits[kRpw - 1] >> 4) & 0xFu, rb, pb);
       }
     }
-  }
-  __syncthreads();
+    __syncthreads();
 
-  // ---- root lists: closed roots to smem, open roots to the tile's record
-  LabelT* T = reinterpret_cast<LabelT*>(b.T);
-  const unsigned lt_mask = (1u << lane) - 1u;
+    // ---- compress the run starts of the warp's rows (only starts can be
+    // roots), and flag clusters that touch the tile edge as open (the edge
+    // sites are spread over all threads)
 #pragma unroll
-  for (int rr = 0; rr < kRpw; ++rr) {
-    const int ly = warp + rr * kWarps;
-    if (ly < h) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int lx = lx0 + k;
-        const uint32_t j = (uint32_t)(ly * kTW + lx);
-        const uint32_t v = lx < w ? P[j] : 0u;
-        const bool isroot = lx < w && (v & kIdx) == j;
-        const bool open = isroot && (v & kOpen);
-        const bool closed = isroot && !(v & kOpen);
-        const unsigned mc = __ballot_sync(kFull, closed);
-        if (mc) {
-          uint32_t base = 0;
-          if (lane == __ffs(mc) - 1) base = atomicAdd(&cnt[0], (uint32_t)__popc(mc));
-          base = __shfl_sync(kFull, base, __ffs(mc) - 1);
-          if (closed) clist[base + __popc(mc & lt_mask)] = (uint16_t)j;
+    for (int rr = 0; rr < kRpw; ++rr) {
+      const int ly = warp * kRpw + rr;
+      if (ly < h) {  // warp-uniform
+        const uint32_t n = warp_enqueue(q, (rowbits[rr] >> 8) & 0xFu, (uint32_t)(ly * kTW), lane);
+        for (uint32_t i = lane; i < n; i += 32) {
+          const uint32_t j = q[i];
+          const uint32_t r = root_masked(P, j, bad);
+          if (r != j) P[j] = r;
         }
-        const unsigned mo = __ballot_sync(kFull, open);
-        if (mo) {
-          uint32_t base = 0;
-          if (lane == __ffs(mo) - 1) base = atomicAdd(&cnt[1], (uint32_t)__popc(mo));
-          base = __shfl_sync(kFull, base, __ffs(mo) - 1);
-          if (open) {
-            b.olist[(uint64_t)t * R::kOpenCap + base + __popc(mo & lt_mask)] = (uint16_t)j;
-            const uint64_t g = global_index(lat, x0, y0, j);
-            T[g] = (LabelT)g;
+        __syncwarp();
+      }
+    }
+    {
+      const int nedge = 2 * (w + h);
+      for (int e = tid; e < nedge; e += kThreads) {
+        int lx, ly;
+        if (e < h) { lx = w - 1; ly = e; }
+        else if (e < 2 * h) { lx = 0; ly = e - h; }
+        else if (e < 2 * h + w) { lx = e - 2 * h; ly = 0; }
+        else { lx = e - 2 * h - w; ly = h - 1; }
+        const uint32_t r = root_masked(P, (uint32_t)(ly * kTW + lx), bad);
+        atomicOr(&P[r], kOpen);
+      }
+    }
+    __syncthreads();
+
+    // ---- root lists, warp-local: a run start j is a root iff P[j] == j.
+    // Closed roots fill the warp's region from the front, open ones from the
+    // back.
+    constexpr int kRegion = kRpw * kTW;
+    uint16_t* wl = clist + warp * kRegion;
+    uint32_t nclosed = 0, nopen = 0;  // warp-uniform
+#pragma unroll
+    for (int rr = 0; rr < kRpw; ++rr) {
+      const int ly = warp * kRpw + rr;
+      if (ly < h) {  // warp-uniform
+        const uint32_t rowbase = (uint32_t)(ly * kTW);
+        const uint32_t stb = (rowbits[rr] >> 8) & 0xFu;
+        uint32_t cm = 0, om = 0;
+        if (stb) {
+          const uint4 v4 = *reinterpret_cast<const uint4*>(P + rowbase + lx0);
+          const uint32_t v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (((stb >> k) & 1u) && (v[k] & kIdx) == rowbase + lx0 + k) {
+              if (v[k] & kOpen) om |= 1u << k; else cm |= 1u << k;
+            }
+          }
+        }
+        const uint32_t mine = (uint32_t)__popc(cm) | ((uint32_t)__popc(om) << 16);
+        uint32_t inc = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(kFull, inc, o);
+          if (lane >= o) inc += y;
+        }
+        const uint32_t excl = inc - mine;
+        uint32_t cpos = nclosed + (excl & 0xFFFFu), opos = nopen + (excl >> 16);
+        while (cm) {
+          const int k = __ffs(cm) - 1;
+          cm &= cm - 1u;
+          wl[cpos++] = (uint16_t)(rowbase + lx0 + k);
+        }
+        while (om) {
+          const int k = __ffs(om) - 1;
+          om &= om - 1u;
+          wl[kRegion - 1 - (opos++)] = (uint16_t)(rowbase + lx0 + k);
+        }
+        const uint32_t total = __shfl_sync(kFull, inc, 31);
+        nclosed += total & 0xFFFFu;
+        nopen += total >> 16;
+      }
+    }
+    if (lane == 0) wcnt[warp] = nclosed | (nopen << 16);
+    __syncthreads();
+
+    // ---- new state of each complete cluster, drawn once at its root; open
+    // roots get their slot in the tile's open list and a global label.  The
+    // per-warp lists are processed as one list by all threads.
+    {
+      uint32_t ctot = 0, otot = 0;
+#pragma unroll
+      for (int w2 = 0; w2 < kWarps; ++w2) {
+        const uint32_t c = wcnt[w2];
+        ctot += c & 0xFFFFu;
+        otot += c >> 16;
+      }
+      if (!kRoots) {
+        for (uint32_t i = tid; i < ctot; i += kThreads) {
+          uint32_t rem = i;
+          int w2 = 0;
+          for (; w2 < kWarps; ++w2) {
+            const uint32_t c = wcnt[w2] & 0xFFFFu;
+            if (rem < c) break;
+            rem -= c;
+          }
+          const uint32_t j = clist[w2 * kRegion + rem];
+          const uint32_t stt = cluster_state(b.seed, global_index(lat, x0, y0, j), sweep, q_states);
+          P[j] = j | (stt << 16);
+        }
+      }
+      for (uint32_t i = tid; i < otot; i += kThreads) {
+        uint32_t rem = i;
+        int w2 = 0;
+        for (; w2 < kWarps; ++w2) {
+          const uint32_t c = wcnt[w2] >> 16;
+          if (rem < c) break;
+          rem -= c;
+        }
+        const uint32_t j = clist[w2 * kRegion + kRegion - 1 - rem];
+        b.olist[(uint64_t)t * R::kOpenCap + i] = (uint16_t)j;
+        P[j] = j | kOpen | (i << 16);
+        const uint64_t g = global_index(lat, x0, y0, j);
+        T[g] = (LabelT)g;
+      }
+      if (tid == 0) b.ocnt[t] = otot;
+    }
+    __syncthreads();
+
+    // ---- per-site codes and the edge lines
+    uint16_t* edge = b.edge + (uint64_t)t * R::kEdge;
+#pragma unroll
+    for (int rr = 0; rr < kRpw; ++rr) {
+      const int ly = warp * kRpw + rr;
+      if (ly < h && lx0 < w) {
+        const uint32_t rowbase = (uint32_t)(ly * kTW);
+        const uint4 v4 = *reinterpret_cast<const uint4*>(P + rowbase + lx0);
+        const uint32_t v[4] = {v4.x, v4.y, v4.z, v4.w};
+        uint32_t c[4], rt[4];
+        uint32_t ps = 0xFFFFFFFFu, pr = 0, pvr = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t x = v[k] & kIdx;  // run start, or the root for a start
+          if (x != ps) {
+            ps = x;
+            pr = P[x] & kIdx;
+            pvr = P[pr];
+          }
+          rt[k] = pr;
+          c[k] = (pvr & kOpen) ? ((pvr >> 16) & 0x1FFu)
+                               : (kRoots ? (kClosed | pr) : (kClosed | ((pvr >> 16) & 0xFFu)));
+        }
+        const uint64_t gi = (y0 + ly) * L + x0 + lx0;
+        if (lat.vec4) {
+          *reinterpret_cast<uint2*>(b.code + gi) = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (lx0 + k < w) b.code[gi + k] = (uint16_t)c[k];
+        }
+        const bool edge_row = (ly == 0 || ly == h - 1);
+        const int last = w - 1 - lx0;
+        if (edge_row || lane == 0 || (last >= 0 && last < 4)) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int lx = lx0 + k;
+            if (lx < w) {
+              if (lx == w - 1) edge[ly] = (uint16_t)rt[k];
+              if (lx == 0) edge[TH + ly] = (uint16_t)rt[k];
+              if (ly == h - 1) edge[2 * TH + lx] = (uint16_t)rt[k];
+              if (ly == 0) edge[2 * TH + kTW + lx] = (uint16_t)rt[k];
+            }
           }
         }
       }
     }
-  }
-  __syncthreads();
-
-  // ---- new state of each complete cluster, drawn once at its root
-  if (!kRoots) {
-    const uint32_t nc = cnt[0];
-    for (uint32_t k = tid; k < nc; k += kThreads) {
-      const uint32_t j = clist[k];
-      const uint32_t st = cluster_state(b.seed, global_index(lat, x0, y0, j), sweep, q);
-      P[j] = j | (st << 16);
-    }
-    __syncthreads();
+    if (tid < R::kBitWords) b.ebits[(uint64_t)t * R::kBitWords + tid] = cbits[tid];
+    __syncthreads();  // smem is reused by the next tile
   }
 
-  // ---- per-site codes and the edge lines
-  uint16_t* edge = b.edge + (uint64_t)t * R::kEdge;
-#pragma unroll
-  for (int rr = 0; rr < kRpw; ++rr) {
-    const int ly = warp + rr * kWarps;
-    if (ly < h && lx0 < w) {
-      uint32_t c[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint32_t j = (uint32_t)(ly * kTW + lx0 + k);
-        const uint32_t r = P[j] & kIdx;
-        const uint32_t vr = P[r];
-        c[k] = (vr & kOpen) ? r : (kRoots ? (kClosed | r) : (kClosed | ((vr >> 16) & 0xFFu)));
-      }
-      const uint64_t gi = (y0 + ly) * L + x0 + lx0;
-      if (lat.vec4) {
-        *reinterpret_cast<uint2*>(b.code + gi) = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
-      } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (lx0 + k < w) b.code[gi + k] = (uint16_t)c[k];
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int lx = lx0 + k;
-        if (lx < w) {
-          if (lx == w - 1) edge[ly] = (uint16_t)c[k];
-          if (lx == 0) edge[TH + ly] = (uint16_t)c[k];
-          if (ly == h - 1) edge[2 * TH + lx] = (uint16_t)c[k];
-          if (ly == 0) edge[2 * TH + kTW + lx] = (uint16_t)c[k];
-        }
-      }
-    }
-  }
-  for (int k = tid; k < R::kBitWords; k += kThreads) b.ebits[(uint64_t)t * R::kBitWords + k] = cbits[k];
-  if (tid == 0) b.ocnt[t] = cnt[1];
-
-  // ---- observables of the configuration read (Sec. 4)
+  // ---- observables of the configuration read (Sec. 4), once per CTA
   if (measure) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e_loc += __shfl_xor_sync(kFull, e_loc, o);
     if (lane == 0) atomicAdd(&sobs[0], e_loc);
     if (qs) {
 #pragma unroll
-      for (uint32_t st = 0; st < 7; ++st) {
+      for (uint32_t st = 0; st < 3; ++st) {
         if (st < qs) {
           uint32_t v = ncnt[st];
 #pragma unroll
@@ -532,15 +755,13 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(const Bufs b, const Lat
       }
     }
     __syncthreads();
-    if (qs) {
-      if (tid == 0) {
-        uint32_t rest = (uint32_t)(w * h);
-        for (uint32_t st = 0; st < qs; ++st) rest -= sobs[1 + st];
-        sobs[1 + qs] = rest;
-      }
-      __syncthreads();
+    if (qs && tid == 0) {
+      uint32_t rest = nsites;
+      for (uint32_t st = 0; st < qs; ++st) rest -= sobs[1 + st];
+      sobs[1 + qs] = rest;
     }
-    for (uint32_t k = tid; k <= q; k += kThreads)
+    __syncthreads();
+    for (uint32_t k = tid; k <= q_states; k += kThreads)
       if (sobs[k]) atomicAdd(&b.acc[k], (unsigned long long)sobs[k]);
   }
   if (bad) atomicOr(b.err, kErrLocal);
@@ -611,13 +832,34 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const Bufs b, const Lat
   }
 }
 
+// ================================================================== k_resolve
+// One thread per open-root slot: find (and compress to) the global root,
+// draw the cluster's new state once per open root (Sec. 2 step (3)).
+template <int TH, typename LabelT>
+__global__ void __launch_bounds__(kMergeThreads) k_resolve(const Bufs b, const Lattice lat) {
+  using R = TileRec<TH>;
+  const uint64_t item = (uint64_t)blockIdx.x * kMergeThreads + threadIdx.x;
+  const uint32_t t = (uint32_t)(item / R::kOpenCap);
+  const uint32_t k = (uint32_t)(item % R::kOpenCap);
+  if (t >= lat.ntiles || k >= b.ocnt[t]) return;
+  uint64_t x0, y0;
+  int w, h;
+  tile_geom(lat, t, TH, x0, y0, w, h);
+  const uint32_t l = b.olist[(uint64_t)t * R::kOpenCap + k];
+  LabelT* T = reinterpret_cast<LabelT*>(b.T);
+  const LabelT r = find_global(T, (LabelT)global_index(lat, x0, y0, l), b.err);
+  b.nso[(uint64_t)t * R::kOpenCap + k] =
+      (uint8_t)cluster_state(b.seed, (uint64_t)r, (uint32_t)b.ctl[1], b.q);
+}
+
 // ================================================================== k_recolor
-// kRoots: write each site's global root (LabelT) to `roots` instead of spins.
+// Streams codes to spins: closed clusters carry their state in the code,
+// open ones index the tile's resolved open-root states.
+// kRoots: write each site's global root (LabelT) to `roots` instead.
 template <int TH, typename LabelT, bool kRoots>
 __global__ void __launch_bounds__(kThreads) k_recolor(const Bufs b, const Lattice lat, LabelT* roots) {
   using R = TileRec<TH>;
   constexpr int kRpw = TH / kWarps;
-  __shared__ uint8_t ns[kRoots ? 1 : kTW * TH];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t t = blockIdx.x;
   uint64_t x0, y0;
@@ -625,17 +867,8 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const Bufs b, const Lattic
   tile_geom(lat, t, TH, x0, y0, w, h);
   const uint64_t L = lat.L;
   LabelT* T = reinterpret_cast<LabelT*>(b.T);
-  const uint32_t sweep = (uint32_t)b.ctl[1];
-  if (!kRoots) {
-    const uint32_t n = b.ocnt[t];
-    const uint16_t* ol = b.olist + (uint64_t)t * R::kOpenCap;
-    for (uint32_t k = tid; k < n; k += kThreads) {
-      const uint32_t l = ol[k];
-      const LabelT r = find_global(T, (LabelT)global_index(lat, x0, y0, l), b.err);
-      ns[l] = (uint8_t)cluster_state(b.seed, (uint64_t)r, sweep, b.q);
-    }
-    __syncthreads();
-  }
+  const uint8_t* nso = b.nso + (uint64_t)t * R::kOpenCap;
+  const uint16_t* ol = b.olist + (uint64_t)t * R::kOpenCap;
   const int lx0 = 4 * lane;
 #pragma unroll
   for (int rr = 0; rr < kRpw; ++rr) {
@@ -644,7 +877,7 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const Bufs b, const Lattic
       const uint64_t gi = (y0 + ly) * L + x0 + lx0;
       uint32_t c[4];
       if (lat.vec4) {
-        const uint2 v = *reinterpret_cast<const uint2*>(b.code + gi);
+        const uint2 v = __ldcs(reinterpret_cast<const uint2*>(b.code + gi));
         c[0] = v.x & 0xFFFFu; c[1] = v.x >> 16; c[2] = v.y & 0xFFFFu; c[3] = v.y >> 16;
       } else {
 #pragma unroll
@@ -654,15 +887,19 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const Bufs b, const Lattic
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           if (lx0 + k < w) {
-            const uint64_t g = global_index(lat, x0, y0, c[k] & kIdx);
-            roots[gi + k] = (c[k] & kClosed) ? (LabelT)g : find_global(T, (LabelT)g, b.err);
+            if (c[k] & kClosed) {
+              roots[gi + k] = (LabelT)global_index(lat, x0, y0, c[k] & kIdx);
+            } else {
+              const uint64_t g = global_index(lat, x0, y0, ol[c[k]]);
+              roots[gi + k] = find_global(T, (LabelT)g, b.err);
+            }
           }
         }
       } else {
         uint32_t s = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const uint32_t v = (c[k] & kClosed) ? (c[k] & 0xFFu) : ns[c[k] & kIdx];
+          const uint32_t v = (c[k] & kClosed) ? (c[k] & 0xFFu) : nso[c[k]];
           s |= v << (8 * k);
         }
         if (lat.vec4) {
