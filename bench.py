@@ -280,6 +280,13 @@ def run_ours(args, rank, world):
                "h2d_bytes_per_step": N, "d2h_bytes_per_step": 8 * (2 + q),
                "steps": args.e2e_steps}
 
+    batched = None
+    if args.batch_sweeps > 0:
+        sim.close()
+        sim = None
+        torch.cuda.empty_cache()
+        batched = run_batched(args, sw, torch)
+
     if rank != 0:
         return 0
     peak, peak_kind = _peaks()
@@ -310,6 +317,7 @@ def run_ours(args, rank, world):
         "update_only": {"value": upd, "unit": UNIT, "steps": args.update_only_steps}
         if upd is not None else None,
         "observables_last": {"config": cfg, "E_sat": E, "n": [int(x) for x in n]},
+        "batched": batched,
     }
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
@@ -317,6 +325,56 @@ def run_ours(args, rank, world):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_batched(args, sw, torch):
+    """Replica sweeps/s of the 512-replica batch (L = 64..2048 log-uniform,
+    q in {2,3,4,5,8}, T in [0.9, 1.1] T_c(q), one Philox key each): all
+    replicas in one batch (autotuned tile height / launch mode) against the
+    same replicas swept one at a time through the single-lattice API."""
+    import numpy as np
+
+    import synth
+    from paper_1208_2080_gb300 import tune
+    p = synth.replica_batch(args.batch_R, master_seed=6)
+    R = args.batch_R
+    cfg = tune.tune_batch(p["L"], p["q"], p["T"], p["seed"])
+    stream = torch.cuda.current_stream()
+    out = {"R": R, "sites": int((p["L"].astype(np.float64) ** 2).sum()), "tuned": cfg}
+    with sw.Batch(p["L"], p["q"], p["T"], p["seed"], tile_h=cfg["tile_h"], graph=cfg["graph"]) as b:
+        b.sweep(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.sweep(args.batch_sweeps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        b.sync()
+        ms = e0.elapsed_time(e1)
+    out.update({"sweeps": args.batch_sweeps, "ms_per_batch_sweep": ms / args.batch_sweeps,
+                "replica_sweeps_per_s": R * args.batch_sweeps / (ms * 1e-3),
+                "spin_updates_per_ns": out["sites"] * args.batch_sweeps / (ms * 1e6)})
+    torch.cuda.empty_cache()
+    sims = [sw.Sim(int(p["L"][r]), int(p["q"][r]), float(p["T"][r]), int(p["seed"][r]))
+            for r in range(R)]
+    for s_ in sims:
+        s_.sweep(2)
+    torch.cuda.synchronize()
+    n1 = args.plain_sweeps
+    e0.record(stream)
+    t0 = time.perf_counter()
+    for s_ in sims:  # one replica at a time
+        s_.sweep(n1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms1 = e0.elapsed_time(e1)
+    for s_ in sims:
+        s_.close()
+    out.update({"plain_sweeps": n1, "plain_replica_sweeps_per_s": R * n1 / (ms1 * 1e-3),
+                "plain_wall_s": wall})
+    out["speedup"] = out["replica_sweeps_per_s"] / out["plain_replica_sweeps_per_s"]
+    return out
 
 
 def main():
@@ -332,6 +390,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--update-only-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-R", type=int, default=512, help="replicas in the batched measurement")
+    ap.add_argument("--batch-sweeps", type=int, default=40, help="0 skips the batched measurement")
+    ap.add_argument("--plain-sweeps", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

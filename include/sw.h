@@ -193,6 +193,69 @@ int sw_label_bonds(uint64_t L, const uint8_t *bonds, void *roots,
 int sw_profile(sw_sim *sim, int enable);
 int sw_profile_read(sw_sim *sim, double *ms, uint64_t *launches, int nphase);
 
+/* ---------------------------------------------------------------------------
+ * Batched replicas (not in the paper: many independent lattices of uneven
+ * L, q and T advanced together).  Every replica follows exactly the single-
+ * lattice conventions above with its own Philox key, so replica r of a batch
+ * reproduces sw_create(L[r], q[r], T[r], seed[r]) bit for bit.  All replicas'
+ * tiles form one work list: a sweep of the whole batch is one persistent
+ * labelling launch plus three short ones, replayed as a CUDA graph.
+ * ------------------------------------------------------------------------- */
+typedef struct sw_batch sw_batch;
+
+typedef struct {
+  uint32_t R;           /* replicas, >= 1 */
+  uint32_t tile_h;      /* 0 = 64, or 16 / 32 / 64 (one tile height for all) */
+  const uint64_t *L;    /* host arrays of R entries: linear sizes (>= 2) */
+  const uint32_t *q;    /*   states (2..255) */
+  const double *T;      /*   temperatures (finite, > 0) */
+  const uint64_t *seed; /*   Philox keys */
+  uint32_t ring;        /* per-replica observable ring, 0 = 64 configurations */
+  uint32_t init;        /* SW_INIT_RANDOM or SW_INIT_ZERO */
+  uint32_t measure;     /* 0 = on, 2 = off */
+  uint32_t graph;       /* 0 = replay sweeps as a CUDA graph, 2 = plain launches */
+  uint32_t reserved[4];
+} sw_batch_params;
+
+typedef struct {
+  uint32_t R;
+  uint32_t tile_h;
+  uint64_t tiles;        /* tiles of all replicas */
+  uint64_t sites;        /* sum of L*L */
+  uint64_t device_bytes; /* device memory held (one arena) */
+  uint32_t label_bits;   /* 32, or 64 if any L > 32768 */
+  uint32_t graph;        /* 1 if sweeps replay a CUDA graph */
+} sw_batch_info_t;
+
+/* Create R replicas (host arrays are read during the call only); one device
+ * arena from the installed allocator.  Errors as for sw_create_ex. */
+int sw_batch_create(uint32_t R, const uint64_t *L, const uint32_t *q,
+                    const double *T, const uint64_t *seed, sw_batch **out);
+int sw_batch_create_ex(const sw_batch_params *params, sw_batch **out);
+void sw_batch_destroy(sw_batch *batch);
+int sw_batch_bind_stream(sw_batch *batch, void *stream);
+/* n sweeps of every replica (asynchronous on the batch's stream). */
+int sw_batch_sweep(sw_batch *batch, uint64_t n);
+/* Per-replica observables, configuration series and spins, as sw_measure /
+ * sw_series / sw_spins / sw_set_spins for replica r < R. */
+int sw_batch_measure(sw_batch *batch, uint32_t r, sw_obs *out);
+int sw_batch_series(sw_batch *batch, uint32_t r, uint64_t first,
+                    uint64_t count, uint64_t *E, uint64_t *n);
+int sw_batch_spins(sw_batch *batch, uint32_t r, uint8_t *dst, uint64_t n,
+                   int dst_on_device);
+int sw_batch_set_spins(sw_batch *batch, uint32_t r, const uint8_t *src,
+                       uint64_t n, int src_on_device);
+/* Sweeps applied to every replica since creation. */
+int sw_batch_get_sweep(const sw_batch *batch, uint64_t *sweep);
+int sw_batch_sync(sw_batch *batch);
+int sw_batch_info(const sw_batch *batch, sw_batch_info_t *out);
+/* Per-phase event timing of batch sweeps (as sw_profile; profiled sweeps
+ * are launched directly, not through the graph). */
+int sw_batch_profile(sw_batch *batch, int enable);
+int sw_batch_profile_read(sw_batch *batch, double *ms, uint64_t *launches,
+                          int nphase);
+int sw_batch_last_error(const sw_batch *batch);
+
 /* Name of an error code. */
 const char *sw_strerror(int code);
 /* Last error recorded on the handle (SW_OK if none). */

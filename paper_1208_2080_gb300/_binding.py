@@ -31,6 +31,10 @@ EXPORTS = [
     "sw_measure", "sw_series", "sw_spins", "sw_set_spins", "sw_bonds", "sw_get_sweep",
     "sw_set_sweep", "sw_sync", "sw_info", "sw_threshold", "sw_label_bonds", "sw_strerror",
     "sw_last_error", "sw_profile", "sw_profile_read",
+    "sw_batch_create", "sw_batch_create_ex", "sw_batch_destroy", "sw_batch_bind_stream",
+    "sw_batch_sweep", "sw_batch_measure", "sw_batch_series", "sw_batch_spins",
+    "sw_batch_set_spins", "sw_batch_get_sweep", "sw_batch_sync", "sw_batch_info",
+    "sw_batch_profile", "sw_batch_profile_read", "sw_batch_last_error",
 ]
 
 
@@ -58,6 +62,20 @@ class sw_info_t(ctypes.Structure):
                 ("label_bits", ctypes.c_uint32), ("tile_w", ctypes.c_uint32),
                 ("tile_h", ctypes.c_uint32), ("ring", ctypes.c_uint32),
                 ("device_bytes", ctypes.c_uint64), ("tiles", ctypes.c_uint64)]
+
+
+class sw_batch_params(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_uint32), ("tile_h", ctypes.c_uint32),
+                ("L", ctypes.POINTER(ctypes.c_uint64)), ("q", ctypes.POINTER(ctypes.c_uint32)),
+                ("T", ctypes.POINTER(ctypes.c_double)), ("seed", ctypes.POINTER(ctypes.c_uint64)),
+                ("ring", ctypes.c_uint32), ("init", ctypes.c_uint32), ("measure", ctypes.c_uint32),
+                ("graph", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 4)]
+
+
+class sw_batch_info_t(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_uint32), ("tile_h", ctypes.c_uint32), ("tiles", ctypes.c_uint64),
+                ("sites", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("label_bits", ctypes.c_uint32), ("graph", ctypes.c_uint32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -100,6 +118,22 @@ def lib():
         "sw_last_error": (i32, [vp]),
         "sw_profile": (i32, [vp, i32]),
         "sw_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), u64p, i32]),
+        "sw_batch_create": (i32, [u32, u64p, ctypes.POINTER(ctypes.c_uint32),
+                                  ctypes.POINTER(ctypes.c_double), u64p, ctypes.POINTER(vp)]),
+        "sw_batch_create_ex": (i32, [ctypes.POINTER(sw_batch_params), ctypes.POINTER(vp)]),
+        "sw_batch_destroy": (None, [vp]),
+        "sw_batch_bind_stream": (i32, [vp, vp]),
+        "sw_batch_sweep": (i32, [vp, u64]),
+        "sw_batch_measure": (i32, [vp, u32, ctypes.POINTER(sw_obs)]),
+        "sw_batch_series": (i32, [vp, u32, u64, u64, u64p, u64p]),
+        "sw_batch_spins": (i32, [vp, u32, vp, u64, i32]),
+        "sw_batch_set_spins": (i32, [vp, u32, vp, u64, i32]),
+        "sw_batch_get_sweep": (i32, [vp, u64p]),
+        "sw_batch_sync": (i32, [vp]),
+        "sw_batch_info": (i32, [vp, ctypes.POINTER(sw_batch_info_t)]),
+        "sw_batch_profile": (i32, [vp, i32]),
+        "sw_batch_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), u64p, i32]),
+        "sw_batch_last_error": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -282,6 +316,105 @@ class Sim:
     @property
     def handle(self):
         return self._h
+
+
+class Batch:
+    """R independent replicas swept together (include/sw.h, sw_batch_*)."""
+
+    def __init__(self, L, q, T, seed, *, tile_h=0, ring=0, init="random", measure=True,
+                 graph=True, stream=None):
+        if not _allocator_chosen:
+            use_torch_allocator()
+        self.L = np.ascontiguousarray(np.asarray(L, dtype=np.uint64))
+        self.q = np.ascontiguousarray(np.asarray(q, dtype=np.uint32))
+        self.T = np.ascontiguousarray(np.asarray(T, dtype=np.float64))
+        self.seed = np.ascontiguousarray(np.asarray(seed, dtype=np.uint64))
+        self.R = len(self.L)
+        p = sw_batch_params()
+        p.R, p.tile_h, p.ring = self.R, int(tile_h), int(ring)
+        p.L = self.L.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        p.q = self.q.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+        p.T = self.T.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        p.seed = self.seed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        p.init = SW_INIT_ZERO if init == "zero" else SW_INIT_RANDOM
+        p.measure = 0 if measure else 2
+        p.graph = 0 if graph else 2
+        h = ctypes.c_void_p()
+        self._h = None
+        check(lib().sw_batch_create_ex(ctypes.byref(p), ctypes.byref(h)), "sw_batch_create_ex")
+        self._h = h
+        if stream is not False:
+            check(lib().sw_batch_bind_stream(self._h, _stream_handle(stream)), "sw_batch_bind_stream")
+
+    def close(self):
+        if self._h is not None:
+            lib().sw_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def sweep(self, n=1):
+        check(lib().sw_batch_sweep(self._h, int(n)), "sw_batch_sweep")
+
+    def sync(self):
+        check(lib().sw_batch_sync(self._h), "sw_batch_sync")
+
+    def measure(self, r):
+        o = sw_obs()
+        check(lib().sw_batch_measure(self._h, int(r), ctypes.byref(o)), "sw_batch_measure")
+        return int(o.E_sat), np.array(o.n[: int(self.q[r])], dtype=np.uint64), int(o.config)
+
+    def series(self, r, first, count):
+        qr = int(self.q[r])
+        E = np.zeros(count, dtype=np.uint64)
+        n = np.zeros((count, qr), dtype=np.uint64)
+        check(lib().sw_batch_series(self._h, int(r), int(first), int(count),
+                                    E.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                    n.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))),
+              "sw_batch_series")
+        return E, n
+
+    def spins(self, r):
+        Lr = int(self.L[r])
+        a = np.empty(Lr * Lr, dtype=np.uint8)
+        check(lib().sw_batch_spins(self._h, int(r), a.ctypes.data_as(ctypes.c_void_p), a.size, 0),
+              "sw_batch_spins")
+        return a.reshape(Lr, Lr)
+
+    def set_spins(self, r, src):
+        a = np.ascontiguousarray(np.asarray(src, dtype=np.uint8).reshape(-1))
+        check(lib().sw_batch_set_spins(self._h, int(r), a.ctypes.data_as(ctypes.c_void_p), a.size,
+                                       0), "sw_batch_set_spins")
+
+    @property
+    def sweep_count(self):
+        v = ctypes.c_uint64()
+        check(lib().sw_batch_get_sweep(self._h, ctypes.byref(v)), "sw_batch_get_sweep")
+        return int(v.value)
+
+    def info(self):
+        i = sw_batch_info_t()
+        check(lib().sw_batch_info(self._h, ctypes.byref(i)), "sw_batch_info")
+        return {k: getattr(i, k) for k, _ in sw_batch_info_t._fields_}
+
+    def profile(self, enable=True):
+        check(lib().sw_batch_profile(self._h, 1 if enable else 0), "sw_batch_profile")
+
+    def profile_read(self):
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_uint64 * 3)()
+        check(lib().sw_batch_profile_read(self._h, ms, n, 3), "sw_batch_profile_read")
+        return list(ms), list(n)
 
 
 def label_bonds(L, bonds_dev, roots_dev, label_bits=32, tile_h=0, stream=None):

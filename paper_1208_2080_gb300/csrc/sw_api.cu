@@ -14,6 +14,7 @@
 #include "../../include/sw.h"
 #include "sw_internal.h"
 #include "sw_kernels.cuh"
+#include "sw_launch.cuh"
 
 using namespace swgb;
 
@@ -76,113 +77,36 @@ size_t edge_u16(uint32_t th) { return 2 * (size_t)th + 2 * kTW; }
 size_t bit_words(uint32_t th) { return (th + 31) / 32 + kTW / 32; }
 size_t open_cap(uint32_t th) { return 2 * (size_t)th + 2 * kTW; }
 
-// ---- launch helpers, instantiated for every tile height / label width
 template <int TH, typename LabelT, bool kGiven, bool kRoots>
 static cudaError_t launch_label_t(const Bufs& b, const Lattice& lat, cudaStream_t st) {
-  auto kern = k_label_tile<TH, LabelT, kGiven, kRoots>;
-  const int smem = LabelSmem<TH>::kBytes;
-  static bool configured = false;  // per instantiation; attribute is per function
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  // persistent grid: as many tile CTAs as fit on the GPU at once
-  static int resident = 0;
-  if (!resident) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TileCta<TH>::kThreads, smem);
-    if (sms <= 0) sms = 152;
-    if (per_sm <= 0) per_sm = 1;
-    resident = sms * per_sm;
-  }
-  const uint32_t grid = lat.ntiles < (uint32_t)resident ? lat.ntiles : (uint32_t)resident;
-  kern<<<grid, TileCta<TH>::kThreads, smem, st>>>(b, lat);
-  return cudaGetLastError();
+  return launch_label_src<TH, LabelT, kGiven, kRoots>(SingleSrc{b, lat}, lat.ntiles, st);
 }
 
 template <int TH, typename LabelT>
 static cudaError_t launch_merge_t(const Bufs& b, const Lattice& lat, cudaStream_t st) {
-  const uint64_t items = (uint64_t)lat.ntiles * (TH + kTW);
-  const uint64_t blocks = (items + kMergeThreads - 1) / kMergeThreads;
-  k_merge<TH, LabelT><<<(unsigned)blocks, kMergeThreads, 0, st>>>(b, lat);
-  return cudaGetLastError();
+  return launch_merge_src<TH, LabelT>(SingleSrc{b, lat}, lat.ntiles, st);
 }
 
 template <int TH, typename LabelT>
 static cudaError_t launch_resolve_t(const Bufs& b, const Lattice& lat, cudaStream_t st) {
-  const uint64_t items = (uint64_t)lat.ntiles * TileRec<TH>::kOpenCap;
-  const uint64_t blocks = (items + kMergeThreads - 1) / kMergeThreads;
-  k_resolve<TH, LabelT><<<(unsigned)blocks, kMergeThreads, 0, st>>>(b, lat);
-  return cudaGetLastError();
+  return launch_resolve_src<TH, LabelT>(SingleSrc{b, lat}, lat.ntiles, st);
 }
 
 template <int TH, typename LabelT, bool kRoots>
 static cudaError_t launch_recolor_t(const Bufs& b, const Lattice& lat, LabelT* roots, cudaStream_t st) {
-  k_recolor<TH, LabelT, kRoots><<<lat.ntiles, kThreads, 0, st>>>(b, lat, roots);
-  return cudaGetLastError();
-}
-
-template <typename LabelT>
-static cudaError_t sweep_once_t(uint32_t th, const Bufs& b, const Lattice& lat, cudaStream_t st) {
-  cudaError_t e;
-  switch (th) {
-#define SWGB_CASE(THV)                                                        \
-  case THV:                                                                   \
-    if ((e = launch_label_t<THV, LabelT, false, false>(b, lat, st))) return e; \
-    if ((e = launch_merge_t<THV, LabelT>(b, lat, st))) return e;              \
-    if ((e = launch_resolve_t<THV, LabelT>(b, lat, st))) return e;            \
-    return launch_recolor_t<THV, LabelT, false>(b, lat, nullptr, st);
-    SWGB_CASE(16)
-    SWGB_CASE(32)
-    SWGB_CASE(64)
-#undef SWGB_CASE
-    default:
-      return cudaErrorInvalidValue;
-  }
-}
-
-// The three launches of one sweep; ev (4 events or null) are recorded
-// before, between and after them.
-template <typename LabelT>
-static cudaError_t sweep_once_ev_t(uint32_t th, const Bufs& b, const Lattice& lat, cudaStream_t st,
-                                   cudaEvent_t* ev) {
-  cudaError_t e;
-  switch (th) {
-#define SWGB_CASE(THV)                                                        \
-  case THV:                                                                   \
-    if ((e = cudaEventRecord(ev[0], st))) return e;                           \
-    if ((e = launch_label_t<THV, LabelT, false, false>(b, lat, st))) return e; \
-    if ((e = cudaEventRecord(ev[1], st))) return e;                           \
-    if ((e = launch_merge_t<THV, LabelT>(b, lat, st))) return e;              \
-    if ((e = launch_resolve_t<THV, LabelT>(b, lat, st))) return e;            \
-    if ((e = cudaEventRecord(ev[2], st))) return e;                           \
-    if ((e = launch_recolor_t<THV, LabelT, false>(b, lat, nullptr, st))) return e; \
-    return cudaEventRecord(ev[3], st);
-    SWGB_CASE(16)
-    SWGB_CASE(32)
-    SWGB_CASE(64)
-#undef SWGB_CASE
-    default:
-      return cudaErrorInvalidValue;
-  }
+  return launch_recolor_src<TH, LabelT, kRoots>(SingleSrc{b, lat}, lat.ntiles, roots, st);
 }
 
 cudaError_t launch_sweep_events(uint32_t label_bits, uint32_t th, const Bufs& b, const Lattice& lat,
                                 cudaStream_t st, cudaEvent_t* ev) {
-  return label_bits == 64 ? sweep_once_ev_t<uint64_t>(th, b, lat, st, ev)
-                          : sweep_once_ev_t<uint32_t>(th, b, lat, st, ev);
+  const SingleSrc src{b, lat};
+  return label_bits == 64 ? sweep_th<uint64_t>(th, src, lat.ntiles, st, ev)
+                          : sweep_th<uint32_t>(th, src, lat.ntiles, st, ev);
 }
 
 cudaError_t launch_sweep(uint32_t label_bits, uint32_t th, const Bufs& b, const Lattice& lat,
                          cudaStream_t st) {
-  return label_bits == 64 ? sweep_once_t<uint64_t>(th, b, lat, st)
-                          : sweep_once_t<uint32_t>(th, b, lat, st);
+  return launch_sweep_events(label_bits, th, b, lat, st, nullptr);
 }
 
 template <typename LabelT>

@@ -120,6 +120,43 @@ struct Bufs {
   uint32_t measure;           // 1: k_label_tile accumulates observables of its input
 };
 
+// A replica of the batched runner: its buffers, geometry and first tile in
+// the concatenated tile list.
+struct Rep {
+  Bufs b;
+  Lattice lat;
+  uint32_t tile0;
+  uint32_t pad_;
+};
+
+// Tile sources: which lattice (and which of its tiles) a global tile id g
+// names.  SingleSrc: one lattice, g is the tile.  BatchSrc: the tiles of R
+// independent replicas (each with its own L, q, T, seed and buffers)
+// concatenated, so one launch sweeps all of them.
+struct SingleSrc {
+  Bufs b;
+  Lattice lat;
+  static constexpr bool kMulti = false;
+  __device__ __forceinline__ uint32_t ntiles() const { return lat.ntiles; }
+  __device__ __forceinline__ uint32_t rep(uint32_t) const { return 0; }
+  __device__ __forceinline__ const Bufs& bufs(uint32_t) const { return b; }
+  __device__ __forceinline__ const Lattice& lattice(uint32_t) const { return lat; }
+  __device__ __forceinline__ uint32_t tile0(uint32_t) const { return 0; }
+};
+
+struct BatchSrc {
+  const Rep* __restrict__ reps;
+  const uint32_t* __restrict__ tile_rep;  // replica of each global tile
+  uint32_t total;                         // tiles of all replicas
+  uint32_t nrep;
+  static constexpr bool kMulti = true;
+  __device__ __forceinline__ uint32_t ntiles() const { return total; }
+  __device__ __forceinline__ uint32_t rep(uint32_t g) const { return __ldg(tile_rep + g); }
+  __device__ __forceinline__ const Bufs& bufs(uint32_t r) const { return reps[r].b; }
+  __device__ __forceinline__ const Lattice& lattice(uint32_t r) const { return reps[r].lat; }
+  __device__ __forceinline__ uint32_t tile0(uint32_t r) const { return reps[r].tile0; }
+};
+
 __device__ __forceinline__ void tile_geom(const Lattice& lat, uint32_t t, int TH, uint64_t& x0,
                                           uint64_t& y0, int& w, int& h) {
   const uint32_t tx = t % lat.ntx, ty = t / lat.ntx;
@@ -328,9 +365,9 @@ __device__ __forceinline__ uint32_t byte_mask(uint32_t nib) {
 // moved with one 16-byte shared-memory access (conflict free); unions and
 // compressions are compacted into per-warp task queues so that all lanes
 // stay busy.
-template <int TH, typename LabelT, bool kGiven, bool kRoots>
+template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src>
 __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks)
-    k_label_tile(const Bufs b, const Lattice lat) {
+    k_label_tile(const __grid_constant__ Src src) {
   static_assert(TH % 16 == 0 && kTW * TH <= 32768, "tile shape");
   using S = LabelSmem<TH>;
   using R = TileRec<TH>;
@@ -352,35 +389,68 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int lx0 = 4 * lane;
   uint16_t* q = wq + warp * kTW;
-  const uint64_t L = lat.L;
-  const uint32_t q_states = b.q;
-  const bool measure = !kGiven && b.measure;
-  const uint32_t sweep = kGiven ? 0u : (uint32_t)b.ctl[0];
+  const uint32_t total = src.ntiles();
   uint32_t bad = 0;
-  LabelT* T = reinterpret_cast<LabelT*>(b.T);
 
-  if (measure)
-    for (int k = tid; k < 257; k += kThreads) sobs[k] = 0;
+  for (int k = tid; k < 257; k += kThreads) sobs[k] = 0;
   uint32_t e_loc = 0, nsites = 0;
   uint32_t ncnt[3] = {0, 0, 0};
-  const uint32_t qs = q_states <= 4 ? q_states - 1 : 0;  // states counted in registers
+
+  // Observables accumulated so far (E_sat, and n[s] for s < q-1 in
+  // registers when q <= 4, else in shared memory) go to the lattice's
+  // accumulator; n[q-1] follows from the site count.  Called by all threads.
+  auto flush = [&](const Bufs& fb, uint32_t fq) {
+    const uint32_t fqs = fq <= 4 ? fq - 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e_loc += __shfl_xor_sync(kFull, e_loc, o);
+    if (lane == 0) atomicAdd(&sobs[0], e_loc);
+    if (fqs) {
+#pragma unroll
+      for (uint32_t st = 0; st < 3; ++st) {
+        if (st < fqs) {
+          uint32_t v = ncnt[st];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+          if (lane == 0) atomicAdd(&sobs[1 + st], v);
+        }
+      }
+    }
+    __syncthreads();
+    if (fqs && tid == 0) {
+      uint32_t rest = nsites;
+      for (uint32_t st = 0; st < fqs; ++st) rest -= sobs[1 + st];
+      sobs[1 + fqs] = rest;
+    }
+    __syncthreads();
+    for (uint32_t k = tid; k <= fq; k += kThreads)
+      if (sobs[k]) atomicAdd(&fb.acc[k], (unsigned long long)sobs[k]);
+    __syncthreads();
+    for (uint32_t k = tid; k <= fq; k += kThreads) sobs[k] = 0;
+    e_loc = 0;
+    nsites = 0;
+    ncnt[0] = ncnt[1] = ncnt[2] = 0;
+  };
 
   // ---- stage a tile's spin rows (0..h-1 and the halo row h) plus each
   // row's halo byte at column w into a shared buffer.  Rows start 4-byte
   // aligned when L % 4 == 0: then the copies are asynchronous (cp.async)
   // and the next tile is staged while this one is labelled.
-  auto stage = [&](uint32_t tt, uint8_t* buf, bool async) {
+  auto stage = [&](uint32_t gg, uint8_t* buf, bool async) {
+    const uint32_t fr = src.rep(gg);
+    const Lattice& fl = src.lattice(fr);
+    const uint8_t* fspin = src.bufs(fr).spin;
+    const uint64_t FL = fl.L;
     uint64_t fx0, fy0;
     int fw, fh;
-    tile_geom(lat, tt, TH, fx0, fy0, fw, fh);
+    tile_geom(fl, gg - src.tile0(fr), TH, fx0, fy0, fw, fh);
     for (int ly = warp; ly <= fh; ly += kWarps) {
-      const uint64_t gy = (ly < fh) ? (fy0 + ly) : ((fy0 + fh) % L);
-      const uint8_t* row = b.spin + gy * L + fx0;
+      const uint64_t gy = (ly < fh) ? (fy0 + ly) : ((fy0 + fh) % FL);
+      const uint8_t* row = fspin + gy * FL + fx0;
       uint8_t* dst = buf + ly * kSpPitch;
       if (async) {
         if (lx0 < fw) cp_async4(dst + lx0, row + lx0);
         // halo column: 4 aligned bytes starting at column (x0 + w) mod L
-        if (lane == 31) cp_async4(dst + fw, b.spin + gy * L + (fx0 + fw) % L);
+        if (lane == 31) cp_async4(dst + fw, fspin + gy * FL + (fx0 + fw) % FL);
       } else {
         uint32_t v = 0;
         if (lx0 < fw) {
@@ -390,32 +460,48 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         }
         *reinterpret_cast<uint32_t*>(dst + lx0) = v;
         __syncwarp();
-        if (lane == 0) dst[fw] = b.spin[gy * L + (fx0 + fw) % L];
+        if (lane == 0) dst[fw] = fspin[gy * FL + (fx0 + fw) % FL];
       }
     }
   };
-  const bool async_stage = !kGiven && lat.vec4;
-  if (async_stage && blockIdx.x < lat.ntiles) {
+  bool pre = false;  // this tile's spins were staged asynchronously
+  if (!kGiven && blockIdx.x < total && src.lattice(src.rep(blockIdx.x)).vec4) {
     stage(blockIdx.x, sp, true);
     cp_async_commit();
+    pre = true;
   }
 
   uint32_t it = 0;
-  for (uint32_t t = blockIdx.x; t < lat.ntiles; t += gridDim.x, ++it) {
+  for (uint32_t g = blockIdx.x; g < total; g += gridDim.x, ++it) {
+    const uint32_t rep = src.rep(g);
+    const Bufs& b = src.bufs(rep);
+    const Lattice& lat = src.lattice(rep);
+    const uint32_t t = g - src.tile0(rep);
+    const uint64_t L = lat.L;
+    const uint32_t q_states = b.q;
+    const bool measure = !kGiven && b.measure;
+    const uint32_t sweep = kGiven ? 0u : (uint32_t)b.ctl[0];
+    const uint32_t qs = q_states <= 4 ? q_states - 1 : 0;  // states counted in registers
+    LabelT* T = reinterpret_cast<LabelT*>(b.T);
     uint64_t x0, y0;
     int w, h;
     tile_geom(lat, t, TH, x0, y0, w, h);
     uint8_t* spc = sp + (it & 1u) * S::kSpBuf;  // this tile's staged spins
     if (tid < R::kBitWords) cbits[tid] = 0;
-    if (async_stage) {
-      cp_async_wait();
-      __syncthreads();  // every thread's copies of this tile have landed
-      if (t + gridDim.x < lat.ntiles) {
-        stage(t + gridDim.x, sp + ((it + 1) & 1u) * S::kSpBuf, true);
-        cp_async_commit();
+    if (!kGiven) {
+      if (pre) {
+        cp_async_wait();
+        __syncthreads();  // every thread's copies of this tile have landed
+      } else {
+        stage(g, spc, false);
       }
-    } else if (!kGiven) {
-      stage(t, spc, false);
+      pre = false;
+      const uint32_t gn = g + gridDim.x;
+      if (gn < total && src.lattice(src.rep(gn)).vec4) {
+        stage(gn, sp + ((it + 1) & 1u) * S::kSpBuf, true);
+        cp_async_commit();
+        pre = true;
+      }
     }
     if (tid == 0) nsites += (uint32_t)(w * h);
     __syncthreads();
@@ -736,51 +822,36 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     }
     if (tid < R::kBitWords) b.ebits[(uint64_t)t * R::kBitWords + tid] = cbits[tid];
     __syncthreads();  // smem is reused by the next tile
+    if (Src::kMulti && measure) flush(b, q_states);  // each tile may belong to another replica
   }
 
   // ---- observables of the configuration read (Sec. 4), once per CTA
-  if (measure) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e_loc += __shfl_xor_sync(kFull, e_loc, o);
-    if (lane == 0) atomicAdd(&sobs[0], e_loc);
-    if (qs) {
-#pragma unroll
-      for (uint32_t st = 0; st < 3; ++st) {
-        if (st < qs) {
-          uint32_t v = ncnt[st];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-          if (lane == 0) atomicAdd(&sobs[1 + st], v);
-        }
-      }
-    }
-    __syncthreads();
-    if (qs && tid == 0) {
-      uint32_t rest = nsites;
-      for (uint32_t st = 0; st < qs; ++st) rest -= sobs[1 + st];
-      sobs[1 + qs] = rest;
-    }
-    __syncthreads();
-    for (uint32_t k = tid; k <= q_states; k += kThreads)
-      if (sobs[k]) atomicAdd(&b.acc[k], (unsigned long long)sobs[k]);
+  if (!Src::kMulti && !kGiven && total > 0 && blockIdx.x < total) {
+    const Bufs& b0 = src.bufs(0);
+    if (b0.measure) flush(b0, b0.q);
   }
-  if (bad) atomicOr(b.err, kErrLocal);
+  if (bad) atomicOr(src.bufs(0).err, kErrLocal);
 }
 
 // ================================================================== k_merge
 // One thread per edge position of every tile: TH right-edge rows, then the
-// 128 bottom-edge columns.  Block 0 / thread 0 also files the observables
-// of the configuration k_label_tile read and advances the sweep counter.
-template <int TH, typename LabelT>
-__global__ void __launch_bounds__(kMergeThreads) k_merge(const Bufs b, const Lattice lat) {
+// 128 bottom-edge columns.  The thread at position 0 of a lattice's tile 0
+// also files the observables of the configuration k_label_tile read and
+// advances that lattice's sweep counter.
+template <int TH, typename LabelT, typename Src>
+__global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__ Src src) {
   using R = TileRec<TH>;
   constexpr int kPer = TH + kTW;
   const uint64_t item = (uint64_t)blockIdx.x * kMergeThreads + threadIdx.x;
-  const uint32_t t = (uint32_t)(item / kPer);
+  const uint32_t g = (uint32_t)(item / kPer);
   const int pos = (int)(item % kPer);
   LabelT a = (LabelT)~(LabelT)0, c = (LabelT)~(LabelT)0;
   bool active = false;
-  if (t < lat.ntiles) {
+  const uint32_t rep = g < src.ntiles() ? src.rep(g) : 0u;
+  const Bufs& b = src.bufs(rep);
+  const Lattice& lat = src.lattice(rep);
+  const uint32_t t = g - src.tile0(rep);
+  if (g < src.ntiles()) {
     uint64_t x0, y0;
     int w, h;
     tile_geom(lat, t, TH, x0, y0, w, h);
@@ -817,7 +888,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const Bufs b, const Lat
   if (active && (int)(threadIdx.x & 31) == __ffs(same) - 1)
     unite_global(reinterpret_cast<LabelT*>(b.T), a, c, b.err);
 
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (g < src.ntiles() && t == 0 && pos == 0) {
     const unsigned long long s = b.ctl[0];
     if (b.measure) {
       unsigned long long* rec = b.ring + (s % b.ring_cap) * (2ull + b.q);
@@ -835,13 +906,18 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const Bufs b, const Lat
 // ================================================================== k_resolve
 // One thread per open-root slot: find (and compress to) the global root,
 // draw the cluster's new state once per open root (Sec. 2 step (3)).
-template <int TH, typename LabelT>
-__global__ void __launch_bounds__(kMergeThreads) k_resolve(const Bufs b, const Lattice lat) {
+template <int TH, typename LabelT, typename Src>
+__global__ void __launch_bounds__(kMergeThreads) k_resolve(const __grid_constant__ Src src) {
   using R = TileRec<TH>;
   const uint64_t item = (uint64_t)blockIdx.x * kMergeThreads + threadIdx.x;
-  const uint32_t t = (uint32_t)(item / R::kOpenCap);
+  const uint32_t g = (uint32_t)(item / R::kOpenCap);
   const uint32_t k = (uint32_t)(item % R::kOpenCap);
-  if (t >= lat.ntiles || k >= b.ocnt[t]) return;
+  if (g >= src.ntiles()) return;
+  const uint32_t rep = src.rep(g);
+  const Bufs& b = src.bufs(rep);
+  const Lattice& lat = src.lattice(rep);
+  const uint32_t t = g - src.tile0(rep);
+  if (k >= b.ocnt[t]) return;
   uint64_t x0, y0;
   int w, h;
   tile_geom(lat, t, TH, x0, y0, w, h);
@@ -856,12 +932,16 @@ __global__ void __launch_bounds__(kMergeThreads) k_resolve(const Bufs b, const L
 // Streams codes to spins: closed clusters carry their state in the code,
 // open ones index the tile's resolved open-root states.
 // kRoots: write each site's global root (LabelT) to `roots` instead.
-template <int TH, typename LabelT, bool kRoots>
-__global__ void __launch_bounds__(kThreads) k_recolor(const Bufs b, const Lattice lat, LabelT* roots) {
+template <int TH, typename LabelT, bool kRoots, typename Src>
+__global__ void __launch_bounds__(kThreads) k_recolor(const __grid_constant__ Src src, LabelT* roots) {
   using R = TileRec<TH>;
   constexpr int kRpw = TH / kWarps;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t t = blockIdx.x;
+  const uint32_t g = blockIdx.x;
+  const uint32_t rep = src.rep(g);
+  const Bufs& b = src.bufs(rep);
+  const Lattice& lat = src.lattice(rep);
+  const uint32_t t = g - src.tile0(rep);
   uint64_t x0, y0;
   int w, h;
   tile_geom(lat, t, TH, x0, y0, w, h);
@@ -915,7 +995,7 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const Bufs b, const Lattic
 }
 
 // ================================================================== init / measure
-__global__ void k_init_spins(uint8_t* s, uint64_t N, uint32_t q, uint64_t seed) {
+static __global__ void k_init_spins(uint8_t* s, uint64_t N, uint32_t q, uint64_t seed) {
   const uint64_t nq = (N + 3) >> 2;
   for (uint64_t qd = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; qd < nq;
        qd += (uint64_t)gridDim.x * blockDim.x) {
@@ -934,7 +1014,7 @@ __global__ void k_init_spins(uint8_t* s, uint64_t N, uint32_t q, uint64_t seed) 
 // E_sat and n[s] of a configuration (the configuration no later sweep reads).
 // One thread per group of 4 sites of a row; 4-byte loads when rows are
 // 4-byte aligned, per-state counts in registers for q <= 8.
-__global__ void __launch_bounds__(256) k_measure(const uint8_t* s, Lattice lat, uint32_t q,
+static __global__ void __launch_bounds__(256) k_measure(const uint8_t* s, Lattice lat, uint32_t q,
                                                  unsigned long long* acc) {
   __shared__ uint32_t hist[257];
   for (int k = threadIdx.x; k < 257; k += blockDim.x) hist[k] = 0;
@@ -1003,7 +1083,7 @@ __global__ void __launch_bounds__(256) k_measure(const uint8_t* s, Lattice lat, 
 }
 
 // Sets *bad if any of the N spins is >= q (validation of a new configuration).
-__global__ void k_check_spins(const uint8_t* s, uint64_t N, uint32_t q, uint32_t* bad) {
+static __global__ void k_check_spins(const uint8_t* s, uint64_t N, uint32_t q, uint32_t* bad) {
   uint32_t any = 0;
   const uint64_t nw = N >> 2;
   const uint32_t lim = q * 0x01010101u;  // q <= 255: per-byte "value >= q" via __vcmpgeu4
@@ -1016,7 +1096,7 @@ __global__ void k_check_spins(const uint8_t* s, uint64_t N, uint32_t q, uint32_t
 }
 
 // Files the accumulated observables as configuration ctl[0].
-__global__ void k_commit(Bufs b) {
+static __global__ void k_commit(Bufs b) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     const unsigned long long s = b.ctl[0];
     unsigned long long* rec = b.ring + (s % b.ring_cap) * (2ull + b.q);
