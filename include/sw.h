@@ -256,6 +256,26 @@ int sw_batch_profile_read(sw_batch *batch, double *ms, uint64_t *launches,
                           int nphase);
 int sw_batch_last_error(const sw_batch *batch);
 
+/* Step (2) alone, like sw_label_bonds, for callers that cannot allocate
+ * device memory: a program whose GPU memory belongs to a framework pool it
+ * cannot borrow from, or one that must not call cudaMalloc/cudaFree once
+ * running (they synchronise the whole device).  The paper has no
+ * counterpart; this is a deployment convenience.
+ * Same inputs and result as sw_label_bonds with label_bits = 32 (bonds and
+ * roots are device pointers, roots receives L*L uint32), but it allocates
+ * nothing: its working memory is one fixed 8 MiB __device__ array in the
+ * library, held by every GPU that loads the library until the process exits.
+ * Lattices larger than SW_LABEL_STATIC_MAX_L are rejected with
+ * SW_ERR_INVAL.  The first call on a device looks up that array's device
+ * address (and configures the kernels); make that first call before any
+ * stream capture.  All calls share the array and the call clears what must
+ * start at zero, so calls that overlap on the GPU (other threads, other
+ * streams) race and must be serialised by the caller.  Runs on `stream` and
+ * synchronises it. */
+#define SW_LABEL_STATIC_MAX_L 1024u
+int sw_label_bonds_static(uint64_t L, const uint8_t *bonds, uint32_t *roots,
+                          uint32_t tile_h, void *stream);
+
 /* Name of an error code. */
 const char *sw_strerror(int code);
 /* Last error recorded on the handle (SW_OK if none). */

@@ -34,7 +34,7 @@ EXPORTS = [
     "sw_batch_create", "sw_batch_create_ex", "sw_batch_destroy", "sw_batch_bind_stream",
     "sw_batch_sweep", "sw_batch_measure", "sw_batch_series", "sw_batch_spins",
     "sw_batch_set_spins", "sw_batch_get_sweep", "sw_batch_sync", "sw_batch_info",
-    "sw_batch_profile", "sw_batch_profile_read", "sw_batch_last_error",
+    "sw_batch_profile", "sw_batch_profile_read", "sw_batch_last_error", "sw_label_bonds_static",
 ]
 
 
@@ -134,6 +134,7 @@ def lib():
         "sw_batch_profile": (i32, [vp, i32]),
         "sw_batch_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), u64p, i32]),
         "sw_batch_last_error": (i32, [vp]),
+        "sw_label_bonds_static": (i32, [u64, vp, vp, u32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -423,6 +424,17 @@ def label_bonds(L, bonds_dev, roots_dev, label_bits=32, tile_h=0, stream=None):
     check(lib().sw_label_bonds(int(L), ctypes.c_void_p(bonds_dev.data_ptr()),
                                ctypes.c_void_p(roots_dev.data_ptr()), int(label_bits),
                                int(tile_h), _stream_handle(stream)), "sw_label_bonds")
+
+
+LABEL_STATIC_MAX_L = 1024
+
+
+def label_bonds_static(L, bonds_dev, roots_dev, tile_h=0, stream=None):
+    """As label_bonds with 32-bit labels, but with no device allocation (the
+    library's fixed working array; L <= LABEL_STATIC_MAX_L)."""
+    check(lib().sw_label_bonds_static(int(L), ctypes.c_void_p(bonds_dev.data_ptr()),
+                                      ctypes.c_void_p(roots_dev.data_ptr()), int(tile_h),
+                                      _stream_handle(stream)), "sw_label_bonds_static")
 
 
 def unpack_bonds(packed, L):
