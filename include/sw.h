@@ -276,6 +276,37 @@ int sw_batch_last_error(const sw_batch *batch);
 int sw_label_bonds_static(uint64_t L, const uint8_t *bonds, uint32_t *roots,
                           uint32_t tile_h, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Surrogate network (not in the paper): a 3 -> 64 -> 64 -> 64 -> 4 tanh MLP
+ * with bfloat16 weights and fp32 accumulation that maps (q, log2 L, T/T_c)
+ * to standardised observables and only places temperature grids.
+ * Parameters are SW_MLP_PARAMS floats, flat, in the order W1[64][3], b1[64],
+ * W2[64][64], b2[64], W3[64][64], b3[64], W4[4][64], b4[4]; every parameter
+ * and every layer input is rounded to bfloat16 before use.  X is B x 3,
+ * outputs / targets / mask are B x 4, row-major fp32 device arrays.
+ * ------------------------------------------------------------------------- */
+#define SW_MLP_PARAMS 8836u
+typedef struct sw_mlp sw_mlp;
+/* init: host array of SW_MLP_PARAMS fp32 master weights (copied). */
+int sw_mlp_create(const float *init, sw_mlp **out);
+void sw_mlp_destroy(sw_mlp *mlp);
+int sw_mlp_bind_stream(sw_mlp *mlp, void *stream);
+/* Y = f(X) for B rows (device pointers; asynchronous). */
+int sw_mlp_forward(sw_mlp *mlp, const float *X, uint32_t B, float *Y);
+/* Gradient of loss = sum(mask*(f(X)-Yt)^2)/(4B) (mask NULL = all ones) into
+ * grad (device, SW_MLP_PARAMS floats) and the loss into *loss (device, may be
+ * NULL); the rounding is treated as the identity in the backward pass. */
+int sw_mlp_gradients(sw_mlp *mlp, const float *X, const float *Yt,
+                     const float *mask, uint32_t B, float *grad, float *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the
+ * fp32 master weights with learning rate lr; refreshes the bfloat16 copy. */
+int sw_mlp_train_step(sw_mlp *mlp, const float *X, const float *Yt,
+                      const float *mask, uint32_t B, float lr, float *loss);
+/* Copy the fp32 master weights and/or their bfloat16 copy to host arrays
+ * (either may be NULL); synchronises.  set_params also resets Adam. */
+int sw_mlp_get_params(sw_mlp *mlp, float *master, uint16_t *bf16);
+int sw_mlp_set_params(sw_mlp *mlp, const float *master);
+
 /* Name of an error code. */
 const char *sw_strerror(int code);
 /* Last error recorded on the handle (SW_OK if none). */

@@ -35,6 +35,8 @@ EXPORTS = [
     "sw_batch_sweep", "sw_batch_measure", "sw_batch_series", "sw_batch_spins",
     "sw_batch_set_spins", "sw_batch_get_sweep", "sw_batch_sync", "sw_batch_info",
     "sw_batch_profile", "sw_batch_profile_read", "sw_batch_last_error", "sw_label_bonds_static",
+    "sw_mlp_create", "sw_mlp_destroy", "sw_mlp_bind_stream", "sw_mlp_forward", "sw_mlp_gradients",
+    "sw_mlp_train_step", "sw_mlp_get_params", "sw_mlp_set_params",
 ]
 
 
@@ -135,6 +137,14 @@ def lib():
         "sw_batch_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), u64p, i32]),
         "sw_batch_last_error": (i32, [vp]),
         "sw_label_bonds_static": (i32, [u64, vp, vp, u32, vp]),
+        "sw_mlp_create": (i32, [vp, ctypes.POINTER(vp)]),
+        "sw_mlp_destroy": (None, [vp]),
+        "sw_mlp_bind_stream": (i32, [vp, vp]),
+        "sw_mlp_forward": (i32, [vp, vp, u32, vp]),
+        "sw_mlp_gradients": (i32, [vp, vp, vp, vp, u32, vp, vp]),
+        "sw_mlp_train_step": (i32, [vp, vp, vp, vp, u32, ctypes.c_float, vp]),
+        "sw_mlp_get_params": (i32, [vp, vp, vp]),
+        "sw_mlp_set_params": (i32, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -424,6 +434,63 @@ def label_bonds(L, bonds_dev, roots_dev, label_bits=32, tile_h=0, stream=None):
     check(lib().sw_label_bonds(int(L), ctypes.c_void_p(bonds_dev.data_ptr()),
                                ctypes.c_void_p(roots_dev.data_ptr()), int(label_bits),
                                int(tile_h), _stream_handle(stream)), "sw_label_bonds")
+
+
+MLP_PARAMS = 8836
+
+
+class Mlp:
+    """The surrogate network on the GPU (include/sw.h, sw_mlp_*).  Tensors
+    passed in are CUDA float32 torch tensors."""
+
+    def __init__(self, init, stream=None):
+        if not _allocator_chosen:
+            use_torch_allocator()
+        a = np.ascontiguousarray(np.asarray(init, dtype=np.float32).reshape(-1))
+        assert a.size == MLP_PARAMS
+        h = ctypes.c_void_p()
+        self._h = None
+        check(lib().sw_mlp_create(a.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)), "sw_mlp_create")
+        self._h = h
+        if stream is not False:
+            check(lib().sw_mlp_bind_stream(self._h, _stream_handle(stream)), "sw_mlp_bind_stream")
+
+    def close(self):
+        if self._h is not None:
+            lib().sw_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _p(t):
+        return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p()
+
+    def forward(self, X, Y):
+        check(lib().sw_mlp_forward(self._h, self._p(X), X.shape[0], self._p(Y)), "sw_mlp_forward")
+
+    def gradients(self, X, Yt, mask, grad, loss=None):
+        check(lib().sw_mlp_gradients(self._h, self._p(X), self._p(Yt), self._p(mask), X.shape[0],
+                                     self._p(grad), self._p(loss)), "sw_mlp_gradients")
+
+    def train_step(self, X, Yt, mask, lr, loss=None):
+        check(lib().sw_mlp_train_step(self._h, self._p(X), self._p(Yt), self._p(mask), X.shape[0],
+                                      float(lr), self._p(loss)), "sw_mlp_train_step")
+
+    def params(self):
+        m = np.empty(MLP_PARAMS, dtype=np.float32)
+        b = np.empty(MLP_PARAMS, dtype=np.uint16)
+        check(lib().sw_mlp_get_params(self._h, m.ctypes.data_as(ctypes.c_void_p),
+                                      b.ctypes.data_as(ctypes.c_void_p)), "sw_mlp_get_params")
+        return m, b
+
+    def set_params(self, master):
+        a = np.ascontiguousarray(np.asarray(master, dtype=np.float32).reshape(-1))
+        check(lib().sw_mlp_set_params(self._h, a.ctypes.data_as(ctypes.c_void_p)), "sw_mlp_set_params")
 
 
 LABEL_STATIC_MAX_L = 1024
