@@ -342,6 +342,15 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// 4-bit mask of the zero bytes of x (bit k <-> byte k).  The per-byte test
+// works on 7-bit lanes, so no carry crosses a byte; the multiply gathers the
+// four byte flags into bits 24..27 (all other partial products fall below
+// bit 24 or beyond bit 31).
+__device__ __forceinline__ uint32_t zero_bytes4(uint32_t x) {
+  const uint32_t t = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
+  return ((t >> 7) * 0x01020408u) >> 24;
+}
+
 __device__ __forceinline__ uint32_t byte_mask(uint32_t nib) {
   // 4-bit site mask -> 0xFF per selected byte
   return ((nib & 1u) ? 0x000000FFu : 0u) | ((nib & 2u) ? 0x0000FF00u : 0u) |
@@ -533,15 +542,14 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         const uint32_t sn = *reinterpret_cast<const uint32_t*>(spc + ly * kSpPitch + lx0 + 4);
         const uint32_t sd = *reinterpret_cast<const uint32_t*>(spc + (ly + 1) * kSpPitch + lx0);
         const uint32_t sr = __funnelshift_r(s, sn, 8);
-        const uint32_t vb = byte_mask(vm);
-        const uint32_t eqr = __vcmpeq4(s, sr) & vb;
-        const uint32_t eqd = __vcmpeq4(s, sd) & vb;
+        const uint32_t eqr = zero_bytes4(s ^ sr) & vm;  // right neighbour has the same state
+        const uint32_t eqd = zero_bytes4(s ^ sd) & vm;  // lower neighbour has the same state
         if (measure) {
-          e_loc += __popc(eqr & 0x01010101u) + __popc(eqd & 0x01010101u);
+          e_loc += __popc(eqr) + __popc(eqd);
           if (qs) {
 #pragma unroll
             for (uint32_t st = 0; st < 3; ++st)
-              if (st < qs) ncnt[st] += __popc(__vcmpeq4(s, st * 0x01010101u) & vb & 0x01010101u);
+              if (st < qs) ncnt[st] += __popc(zero_bytes4(s ^ (st * 0x01010101u)) & vm);
           } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
@@ -562,11 +570,15 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
             wr[0] = A.z; wd[0] = A.w; wr[1] = B.x; wd[1] = B.y;
             wr[2] = B.z; wd[2] = B.w; wr[3] = C.x; wd[3] = C.y;
           }
+          const uint32_t thr = b.thr;
+          uint32_t ur = 0, ud = 0;  // u < thr per site
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            br |= (((eqr >> (8 * k)) & 1u) & (wr[k] < b.thr ? 1u : 0u)) << k;
-            bd |= (((eqd >> (8 * k)) & 1u) & (wd[k] < b.thr ? 1u : 0u)) << k;
+            ur |= (wr[k] < thr ? 1u : 0u) << k;
+            ud |= (wd[k] < thr ? 1u : 0u) << k;
           }
+          br = eqr & ur;
+          bd = eqd & ud;
         }
         if (b.bonds && vm) {
           uint32_t byte = 0;
@@ -601,13 +613,13 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
       const int src = below ? 31 - __clz(below) : 0;
       const int lbs = __shfl_sync(kFull, lb, src);
       const uint32_t rowbase = (uint32_t)(ly * kTW);
-      uint32_t st4[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint32_t m = brk & ((2u << k) - 1u);
-        st4[k] = rowbase + (uint32_t)(m ? lx0 + 31 - __clz(m) : 4 * src + lbs);
-      }
-      *reinterpret_cast<uint4*>(P + rowbase + lx0) = make_uint4(st4[0], st4[1], st4[2], st4[3]);
+      // run start of each site: itself if it breaks the run, else the start
+      // of the site to its left (the first site inherits from earlier lanes)
+      const uint32_t st0 = rowbase + ((brk & 1u) ? (uint32_t)lx0 : (uint32_t)(4 * src + lbs));
+      const uint32_t st1 = (brk & 2u) ? rowbase + lx0 + 1 : st0;
+      const uint32_t st2 = (brk & 4u) ? rowbase + lx0 + 2 : st1;
+      const uint32_t st3 = (brk & 8u) ? rowbase + lx0 + 3 : st2;
+      *reinterpret_cast<uint4*>(P + rowbase + lx0) = make_uint4(st0, st1, st2, st3);
       rbn[ly * 32 + lane] = (uint8_t)r4;
     }
     __syncthreads();
@@ -1046,12 +1058,13 @@ static __global__ void __launch_bounds__(256) k_measure(const uint8_t* s, Lattic
         vm |= 0xFFu << (8 * k);
       }
     }
-    e += __popc(__vcmpeq4(v, vr) & vm & 0x01010101u) + __popc(__vcmpeq4(v, vd) & vm & 0x01010101u);
-    nsites += __popc(vm & 0x01010101u);
+    const uint32_t vn = zero_bytes4(~vm);  // valid sites of the group
+    e += __popc(zero_bytes4(v ^ vr) & vn) + __popc(zero_bytes4(v ^ vd) & vn);
+    nsites += __popc(vn);
     if (qs) {
 #pragma unroll
       for (uint32_t st = 0; st < 7; ++st)
-        if (st < qs) cnt[st] += __popc(__vcmpeq4(v, st * 0x01010101u) & vm & 0x01010101u);
+        if (st < qs) cnt[st] += __popc(zero_bytes4(v ^ (st * 0x01010101u)) & vn);
     } else {
       for (int k = 0; k < 4; ++k)
         if ((vm >> (8 * k)) & 1u) atomicAdd(&hist[1 + ((v >> (8 * k)) & 0xFFu)], 1u);
