@@ -130,10 +130,8 @@ static cudaError_t label_given_t(uint32_t th, const Bufs& b, const Lattice& lat,
 
 cudaError_t launch_measure(const uint8_t* spin, const Lattice& lat, uint32_t q,
                            const Bufs& b, cudaStream_t st) {
-  const uint64_t total = ((lat.L + 3) / 4) * lat.L;
-  uint64_t blocks = (total + 255) / 256;
+  uint64_t blocks = lat.L;  // one block per row, at most 16 per SM
   if (blocks > 152ull * 16) blocks = 152ull * 16;
-  if (blocks == 0) blocks = 1;
   k_measure<<<(unsigned)blocks, 256, 0, st>>>(spin, lat, q, b.acc);
   cudaError_t e = cudaGetLastError();
   if (e) return e;

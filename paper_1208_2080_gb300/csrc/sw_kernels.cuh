@@ -452,24 +452,27 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     uint64_t fx0, fy0;
     int fw, fh;
     tile_geom(fl, gg - src.tile0(fr), TH, fx0, fy0, fw, fh);
+    // halo row and column wrap around the lattice (x0 + w <= L, y0 + h <= L)
+    const uint64_t hx = (fx0 + fw == FL) ? 0 : fx0 + fw;
+    const uint64_t hy = (fy0 + fh == FL) ? 0 : fy0 + fh;
     for (int ly = warp; ly <= fh; ly += kWarps) {
-      const uint64_t gy = (ly < fh) ? (fy0 + ly) : ((fy0 + fh) % FL);
-      const uint8_t* row = fspin + gy * FL + fx0;
+      const uint64_t gy = (ly < fh) ? (fy0 + ly) : hy;
+      const uint8_t* row = fspin + gy * FL;
       uint8_t* dst = buf + ly * kSpPitch;
       if (async) {
-        if (lx0 < fw) cp_async4(dst + lx0, row + lx0);
+        if (lx0 < fw) cp_async4(dst + lx0, row + fx0 + lx0);
         // halo column: 4 aligned bytes starting at column (x0 + w) mod L
-        if (lane == 31) cp_async4(dst + fw, fspin + gy * FL + (fx0 + fw) % FL);
+        if (lane == 31) cp_async4(dst + fw, row + hx);
       } else {
         uint32_t v = 0;
         if (lx0 < fw) {
 #pragma unroll
           for (int k = 0; k < 4; ++k)
-            if (lx0 + k < fw) v |= (uint32_t)row[lx0 + k] << (8 * k);
+            if (lx0 + k < fw) v |= (uint32_t)row[fx0 + lx0 + k] << (8 * k);
         }
         *reinterpret_cast<uint32_t*>(dst + lx0) = v;
         __syncwarp();
-        if (lane == 0) dst[fw] = fspin[gy * FL + (fx0 + fw) % FL];
+        if (lane == 0) dst[fw] = row[hx];
       }
     }
   };
@@ -1033,41 +1036,42 @@ static __global__ void __launch_bounds__(256) k_measure(const uint8_t* s, Lattic
   __syncthreads();
   const uint64_t L = lat.L;
   const uint64_t groups = (L + 3) >> 2;
-  const uint64_t total = groups * L;
   const uint32_t qs = q <= 8 ? q - 1 : 0;
   uint32_t e = 0, cnt[7] = {0, 0, 0, 0, 0, 0, 0}, nsites = 0;
-  for (uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
-       it += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t y = it / groups, x = (it % groups) * 4;
+  // rows over blocks, 4-site groups of a row over threads
+  for (uint64_t y = blockIdx.x; y < L; y += gridDim.x) {
     const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
-    uint32_t v, vr, vd, vm;
-    if (lat.vec4) {
-      v = *reinterpret_cast<const uint32_t*>(s + y * L + x);
-      const uint64_t xn = (x + 4 == L) ? 0 : x + 4;
-      const uint32_t vn = *reinterpret_cast<const uint32_t*>(s + y * L + xn);
-      vr = __funnelshift_r(v, vn, 8);
-      vd = *reinterpret_cast<const uint32_t*>(s + yd * L + x);
-      vm = 0xFFFFFFFFu;
-    } else {
-      v = vr = vd = vm = 0;
-      for (int k = 0; k < 4 && x + k < L; ++k) {
-        const uint64_t xk = x + k, xr = (xk + 1 == L) ? 0 : xk + 1;
-        v |= (uint32_t)s[y * L + xk] << (8 * k);
-        vr |= (uint32_t)s[y * L + xr] << (8 * k);
-        vd |= (uint32_t)s[yd * L + xk] << (8 * k);
-        vm |= 0xFFu << (8 * k);
+    for (uint64_t gx = threadIdx.x; gx < groups; gx += blockDim.x) {
+      const uint64_t x = gx * 4;
+      uint32_t v, vr, vd, vm;
+      if (lat.vec4) {
+        v = *reinterpret_cast<const uint32_t*>(s + y * L + x);
+        const uint64_t xn = (x + 4 == L) ? 0 : x + 4;
+        const uint32_t vn = *reinterpret_cast<const uint32_t*>(s + y * L + xn);
+        vr = __funnelshift_r(v, vn, 8);
+        vd = *reinterpret_cast<const uint32_t*>(s + yd * L + x);
+        vm = 0xFFFFFFFFu;
+      } else {
+        v = vr = vd = vm = 0;
+        for (int k = 0; k < 4 && x + k < L; ++k) {
+          const uint64_t xk = x + k, xr = (xk + 1 == L) ? 0 : xk + 1;
+          v |= (uint32_t)s[y * L + xk] << (8 * k);
+          vr |= (uint32_t)s[y * L + xr] << (8 * k);
+          vd |= (uint32_t)s[yd * L + xk] << (8 * k);
+          vm |= 0xFFu << (8 * k);
+        }
       }
-    }
-    const uint32_t vn = zero_bytes4(~vm);  // valid sites of the group
-    e += __popc(zero_bytes4(v ^ vr) & vn) + __popc(zero_bytes4(v ^ vd) & vn);
-    nsites += __popc(vn);
-    if (qs) {
+      const uint32_t vnib = zero_bytes4(~vm);  // valid sites of the group
+      e += __popc(zero_bytes4(v ^ vr) & vnib) + __popc(zero_bytes4(v ^ vd) & vnib);
+      nsites += __popc(vnib);
+      if (qs) {
 #pragma unroll
-      for (uint32_t st = 0; st < 7; ++st)
-        if (st < qs) cnt[st] += __popc(zero_bytes4(v ^ (st * 0x01010101u)) & vn);
-    } else {
-      for (int k = 0; k < 4; ++k)
-        if ((vm >> (8 * k)) & 1u) atomicAdd(&hist[1 + ((v >> (8 * k)) & 0xFFu)], 1u);
+        for (uint32_t st = 0; st < 7; ++st)
+          if (st < qs) cnt[st] += __popc(zero_bytes4(v ^ (st * 0x01010101u)) & vnib);
+      } else {
+        for (int k = 0; k < 4; ++k)
+          if ((vm >> (8 * k)) & 1u) atomicAdd(&hist[1 + ((v >> (8 * k)) & 0xFFu)], 1u);
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {

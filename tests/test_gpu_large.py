@@ -1,0 +1,105 @@
+"""Parity at the production size, q=2, T_c, L=65536 (4.29e9 sites, uint64
+labels), all-zero start, in the configuration bench.py times: the oracle
+cannot sweep the whole lattice in a test, so it checks sampled outputs one by
+one and the observables are recounted independently:
+  * E_sat and n[s] recounted from the spins with plain torch ops;
+  * sampled sites whose cluster is small: the cluster is found by a bounded
+    breadth-first search over bonds computed site by site with the oracle's
+    Philox and threshold from the configuration before the sweep; every
+    member's new spin must be the oracle's pick for the cluster's smallest
+    site index."""
+from collections import deque
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1208_2080_gb300 as sw
+
+pytestmark = pytest.mark.gpu
+
+L = 65536
+Q = 2
+SEED = 5
+
+
+def _word(seed, idx, sweep, dom, word):
+    return int(oracle.philox([idx & 0xFFFFFFFF, idx >> 32, sweep, dom],
+                             [seed & 0xFFFFFFFF, seed >> 32])[word])
+
+
+def _bond(spins_at, i, d, thr, sweep):
+    """Bond d (0 right, 1 down) owned by site i, from the oracle's streams."""
+    y, x = divmod(i, L)
+    j = y * L + (x + 1) % L if d == 0 else ((y + 1) % L) * L + x
+    if spins_at(i) != spins_at(j):
+        return False, j
+    return _word(SEED, i >> 1, sweep, 0, 2 * (i & 1) + d) < thr, j
+
+
+def _cluster(spins_at, i, thr, sweep, cap=48):
+    """Members of i's cluster if it has at most `cap` sites, else None."""
+    seen, dq = {i}, deque([i])
+    while dq:
+        u = dq.popleft()
+        y, x = divmod(u, L)
+        left = y * L + (x - 1) % L
+        up = ((y - 1) % L) * L + x
+        for owner, d, other in ((u, 0, None), (u, 1, None), (left, 0, u), (up, 1, u)):
+            on, j = _bond(spins_at, owner, d, thr, sweep)
+            v = owner if other is not None else j
+            if on and v not in seen:
+                seen.add(v)
+                dq.append(v)
+                if len(seen) > cap:
+                    return None
+    return seen
+
+
+def _check_sweep(before_at, after, thr, sweep, rng, want=150):
+    ok = 0
+    tries = 0
+    while ok < want and tries < 40 * want:
+        tries += 1
+        i = int(rng.integers(0, L * L))
+        c = _cluster(before_at, i, thr, sweep)
+        if c is None:
+            continue
+        r = min(c)
+        s = oracle.pick(_word(SEED, r, sweep, 1, 0), Q)
+        for v in c:
+            assert after[v // L, v % L] == s, (sweep, i, v, r)
+        ok += 1
+    assert ok >= want // 2, f"only {ok} small clusters sampled"
+
+
+def _recount(spins_dev):
+    import torch
+    s = spins_dev.view(L, L)
+    E = int((s == torch.roll(s, -1, 1)).sum().item()) + int((s == torch.roll(s, -1, 0)).sum().item())
+    n = [int((s == k).sum().item()) for k in range(Q)]
+    return E, n
+
+
+def test_production_size_two_sweeps():
+    import torch
+    rng = np.random.default_rng(2024)
+    thr = oracle.threshold(sw.tc(Q))
+    with sw.Sim(L, Q, sw.tc(Q), SEED, init="zero") as sim:
+        assert sim.info()["label_bits"] == 64
+        assert sim.info()["thr"] == thr
+        sim.sweep(1)
+        first = sim.spins()
+        _check_sweep(lambda i: 0, first, thr, 0, rng)
+        sim.sweep(1)
+        second = sim.spins()
+        _check_sweep(lambda i: int(first[i // L, i % L]), second, thr, 1, rng)
+        E, n, c = sim.measure()
+        assert c == 2 and sum(int(x) for x in n) == L * L
+        dev = torch.from_numpy(second.reshape(-1)).cuda()
+        assert _recount(dev) == (E, [int(x) for x in n])
+        E1, n1 = sim.series(1, 1)
+        assert _recount(torch.from_numpy(first.reshape(-1)).cuda()) == (int(E1[0]),
+                                                                        [int(x) for x in n1[0]])
+    del dev
+    torch.cuda.empty_cache()
