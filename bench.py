@@ -134,6 +134,22 @@ def _traffic(kernel, L):
         return None
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The slowest rank's time (every rank gets it); ms itself on one rank."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(sites_per_rank, steps, world, max_ms):
+    """Whole-job spin updates per ns: every rank sweeps its own lattice
+    (replicas, no exchange), timed by the slowest rank."""
+    return sites_per_rank * steps * world / (max_ms * 1e6)
+
+
 def cpu_baseline(seconds=15.0, L=8192):
     """The oracle, as it stands, single-threaded on a bounded sample: q=2,
     T_c, L x L from the init stream, as many sweeps as fit in ~`seconds`."""
@@ -224,13 +240,10 @@ def run_ours(args, rank, world):
     ms = ev0.elapsed_time(ev1)
     phase_ms, phase_n = sim.profile_read()
     sim.profile(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, device="cuda")
     E, n, cfg = sim.measure()
     assert int(n.sum()) == N and 0 <= E <= 2 * N, "observables out of range"
-    value = N * args.steps * world / (ms * 1e6)
+    value = job_rate(N, args.steps, world, ms)
 
     # update only (Table 1's other column): same chain with measurement off
     upd = None

@@ -256,6 +256,20 @@ int sw_batch_profile_read(sw_batch *batch, double *ms, uint64_t *launches,
                           int nphase);
 int sw_batch_last_error(const sw_batch *batch);
 
+/* The paper's labeller (Sec. 2: label equivalence after Kalentev et al.),
+ * for comparison with sw_label_bonds: every site starts labelled with its
+ * own index; a scanning pass lowers label[label[i]] to the smallest label
+ * among i's active-bond neighbours, an analysis pass makes every site adopt
+ * the end of its label chain; both repeat until a scan changes nothing.
+ * Same inputs and result as sw_label_bonds (bit-identical roots).
+ * *iterations (may be NULL) receives the number of scan+analysis rounds,
+ * the last one being the round that found nothing to change; more than
+ * max_iter rounds (0 = no practical limit) returns SW_ERR_TIMEOUT.  Reads a
+ * flag back after every round; synchronises `stream`. */
+int sw_label_bonds_le(uint64_t L, const uint8_t *bonds, void *roots,
+                      uint32_t label_bits, uint32_t max_iter,
+                      uint32_t *iterations, void *stream);
+
 /* Step (2) alone, like sw_label_bonds, for callers that cannot allocate
  * device memory: a program whose GPU memory belongs to a framework pool it
  * cannot borrow from, or one that must not call cudaMalloc/cudaFree once

@@ -36,7 +36,7 @@ EXPORTS = [
     "sw_batch_set_spins", "sw_batch_get_sweep", "sw_batch_sync", "sw_batch_info",
     "sw_batch_profile", "sw_batch_profile_read", "sw_batch_last_error", "sw_label_bonds_static",
     "sw_mlp_create", "sw_mlp_destroy", "sw_mlp_bind_stream", "sw_mlp_forward", "sw_mlp_gradients",
-    "sw_mlp_train_step", "sw_mlp_get_params", "sw_mlp_set_params",
+    "sw_mlp_train_step", "sw_mlp_get_params", "sw_mlp_set_params", "sw_label_bonds_le",
 ]
 
 
@@ -145,6 +145,7 @@ def lib():
         "sw_mlp_train_step": (i32, [vp, vp, vp, vp, u32, ctypes.c_float, vp]),
         "sw_mlp_get_params": (i32, [vp, vp, vp]),
         "sw_mlp_set_params": (i32, [vp, vp]),
+        "sw_label_bonds_le": (i32, [u64, vp, vp, u32, u32, ctypes.POINTER(ctypes.c_uint32), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -494,6 +495,17 @@ class Mlp:
 
 
 LABEL_STATIC_MAX_L = 1024
+
+
+def label_bonds_le(L, bonds_dev, roots_dev, label_bits=32, max_iter=0, stream=None):
+    """The paper's label-equivalence labeller on device buffers; returns the
+    number of scan/analysis rounds it took."""
+    it = ctypes.c_uint32()
+    check(lib().sw_label_bonds_le(int(L), ctypes.c_void_p(bonds_dev.data_ptr()),
+                                  ctypes.c_void_p(roots_dev.data_ptr()), int(label_bits),
+                                  int(max_iter), ctypes.byref(it), _stream_handle(stream)),
+          "sw_label_bonds_le")
+    return int(it.value)
 
 
 def label_bonds_static(L, bonds_dev, roots_dev, tile_h=0, stream=None):
