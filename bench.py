@@ -119,9 +119,10 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel, L):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+def _profile_figure(kernel, key, L):
+    """Per-launch figure (`key` per site x sites) of `kernel` from the
+    committed ncu summary, if it was taken on the current kernel source
+    (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -129,9 +130,19 @@ def _traffic(kernel, L):
         e = d[kernel]
         if e.get("source_hash") != _kernel_hash():
             return None
-        return float(e["bytes_per_site"]) * L * L
+        return float(e[key]) * L * L
     except Exception:
         return None
+
+
+def _traffic(kernel, L):
+    """DRAM bytes per launch of `kernel` (ncu), or None."""
+    return _profile_figure(kernel, "bytes_per_site", L)
+
+
+# Instruction issue peak of the GPU: 4 warp instructions per clock per SM
+# (four schedulers), 152 SMs, 2070 MHz maximum SM clock.
+ISSUE_PEAK = 4 * 152 * 2070e6
 
 
 def max_over_ranks(ms, dist=None, device="cpu"):
@@ -312,6 +323,14 @@ def run_ours(args, rank, world):
             "frac": achieved / peak, "peak_kind": peak_kind, "traffic": _traffic(name, L),
             "alg_bytes_per_launch": alg, "avg_launch_ms": avg[dom],
             "phase_ms_per_sweep": {PHASES[k]: avg[k] for k in range(3)}}
+    # the tile kernel is bound by instruction issue, not by HBM: its issue
+    # rate against the GPU's issue peak (instruction count per site from ncu)
+    winst = _profile_figure(name, "warp_inst_per_site", L)
+    if winst is not None:
+        rate = winst / (avg[dom] * 1e-3)
+        roof["issue"] = {"bound": "issue", "achieved": rate, "peak": ISSUE_PEAK,
+                         "unit": "warp instructions/s", "frac": rate / ISSUE_PEAK,
+                         "warp_inst_per_launch": winst}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
