@@ -745,42 +745,33 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     if (lane == 0) wcnt[warp] = nclosed | (nopen << 16);
     __syncthreads();
 
-    // ---- new state of each complete cluster, drawn once at its root; open
-    // roots get their slot in the tile's open list and a global label.  The
-    // per-warp lists are processed as one list by all threads.
+    // ---- new state of each complete cluster, drawn once at its root, by the
+    // warp that listed it; open roots get their slot in the tile's open
+    // list (warp by warp) and a global label
     {
-      uint32_t ctot = 0, otot = 0;
+      uint32_t obase = 0, otot = 0;
+      if (lane < kWarps) {
+        const uint32_t c = wcnt[lane] >> 16;
+        obase = lane < warp ? c : 0u;
+        otot = c;
+      }
 #pragma unroll
-      for (int w2 = 0; w2 < kWarps; ++w2) {
-        const uint32_t c = wcnt[w2];
-        ctot += c & 0xFFFFu;
-        otot += c >> 16;
+      for (int o = 16; o > 0; o >>= 1) {
+        obase += __shfl_xor_sync(kFull, obase, o);
+        otot += __shfl_xor_sync(kFull, otot, o);
       }
       if (!kRoots) {
-        for (uint32_t i = tid; i < ctot; i += kThreads) {
-          uint32_t rem = i;
-          int w2 = 0;
-          for (; w2 < kWarps; ++w2) {
-            const uint32_t c = wcnt[w2] & 0xFFFFu;
-            if (rem < c) break;
-            rem -= c;
-          }
-          const uint32_t j = clist[w2 * kRegion + rem];
+        for (uint32_t i = lane; i < nclosed; i += 32) {
+          const uint32_t j = wl[i];
           const uint32_t stt = cluster_state(b.seed, global_index(lat, x0, y0, j), sweep, q_states);
           P[j] = j | (stt << 16);
         }
       }
-      for (uint32_t i = tid; i < otot; i += kThreads) {
-        uint32_t rem = i;
-        int w2 = 0;
-        for (; w2 < kWarps; ++w2) {
-          const uint32_t c = wcnt[w2] >> 16;
-          if (rem < c) break;
-          rem -= c;
-        }
-        const uint32_t j = clist[w2 * kRegion + kRegion - 1 - rem];
-        b.olist[(uint64_t)t * R::kOpenCap + i] = (uint16_t)j;
-        P[j] = j | kOpen | (i << 16);
+      for (uint32_t i = lane; i < nopen; i += 32) {
+        const uint32_t j = wl[kRegion - 1 - i];
+        const uint32_t slot = obase + i;
+        b.olist[(uint64_t)t * R::kOpenCap + slot] = (uint16_t)j;
+        P[j] = j | kOpen | (slot << 16);
         const uint64_t g = global_index(lat, x0, y0, j);
         T[g] = (LabelT)g;
       }
