@@ -248,3 +248,33 @@ def test_large_lattice_properties():
         ref, refE, refn = oracle.run(L, q, sw.tc(q), 2 + q, n)
         assert np.array_equal(E, refE) and np.array_equal(nn, refn)
         assert np.array_equal(got, ref)
+
+
+GOLDEN_8192 = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden",
+                                         "l8192_q234.json")
+
+
+@pytest.mark.skipif(not __import__("os").path.exists(GOLDEN_8192),
+                    reason="L=8192 golden values not generated")
+def test_config_l8192_q234_1200_sweeps_match_oracle():
+    """q = 2, 3, 4 at T_c, L = 8192, 200 + 1000 sweeps: spins after sweeps 200
+    and 1200 and the whole per-sweep E_sat / n[s] series equal the oracle's
+    (SHA-256 digests from tests/golden/make_l8192_golden.py, which calls only
+    the oracle); the measured energy approaches Baxter's -(1 + 1/sqrt q)."""
+    import hashlib
+    import json
+    gold = json.load(open(GOLDEN_8192))
+    h = lambda a: hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+    for g in gold["runs"]:
+        q, L = g["q"], g["L"]
+        assert sw.threshold(sw.tc(q)) == g["thr"]
+        with sw.Sim(L, q, sw.tc(q), g["seed"], ring=1300) as s:
+            s.sweep(200)
+            assert h(s.spins()) == g["spins200_sha256"], q
+            s.sweep(1000)
+            assert h(s.spins()) == g["spins1200_sha256"], q
+            E, n = s.series(1, 1200)
+        assert h(E.astype("<u8")) == g["E_sha256"] and h(n.astype("<u8")) == g["n_sha256"], q
+        u = -(E[200:].astype(np.float64) / (L * L)).mean()
+        assert abs(u - g["u_mean"]) < 1e-12
+        assert abs(u + (1 + 1 / np.sqrt(q))) < {2: 2e-3, 3: 5e-3, 4: 1.5e-2}[q]
