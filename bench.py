@@ -203,8 +203,10 @@ def run_reference(args, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": f"q=2 Ising at T_c, all-zero start; oracle sample L={L} "
-                               f"(bench workload L=65536)", "L": L, "q": 2},
+        "config": {"workload": f"q=2 Ising, L={args.L}, T=T_c, all-zero start, "
+                               f"uint{64 if args.L > 32768 else 32} labels, sweeps {args.warmup}.."
+                               f"{args.warmup + args.steps - 1}",
+                   "L": args.L, "q": 2, "oracle_sample_L": L},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
