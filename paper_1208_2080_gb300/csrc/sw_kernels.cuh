@@ -910,28 +910,30 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__
 }
 
 // ================================================================== k_resolve
-// One thread per open-root slot: find (and compress to) the global root,
-// draw the cluster's new state once per open root (Sec. 2 step (3)).
+// One warp per tile, a lane per open root: find (and compress to) the global
+// root, draw the cluster's new state once per open root (Sec. 2 step (3)).
 template <int TH, typename LabelT, typename Src>
 __global__ void __launch_bounds__(kMergeThreads) k_resolve(const __grid_constant__ Src src) {
   using R = TileRec<TH>;
-  const uint64_t item = (uint64_t)blockIdx.x * kMergeThreads + threadIdx.x;
-  const uint32_t g = (uint32_t)(item / R::kOpenCap);
-  const uint32_t k = (uint32_t)(item % R::kOpenCap);
+  const uint64_t g = ((uint64_t)blockIdx.x * kMergeThreads + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31u;
   if (g >= src.ntiles()) return;
-  const uint32_t rep = src.rep(g);
+  const uint32_t rep = src.rep((uint32_t)g);
   const Bufs& b = src.bufs(rep);
   const Lattice& lat = src.lattice(rep);
-  const uint32_t t = g - src.tile0(rep);
-  if (k >= b.ocnt[t]) return;
+  const uint32_t t = (uint32_t)g - src.tile0(rep);
+  const uint32_t n = b.ocnt[t];
+  if (lane >= n) return;
   uint64_t x0, y0;
   int w, h;
   tile_geom(lat, t, TH, x0, y0, w, h);
-  const uint32_t l = b.olist[(uint64_t)t * R::kOpenCap + k];
   LabelT* T = reinterpret_cast<LabelT*>(b.T);
-  const LabelT r = find_global(T, (LabelT)global_index(lat, x0, y0, l), b.err);
-  b.nso[(uint64_t)t * R::kOpenCap + k] =
-      (uint8_t)cluster_state(b.seed, (uint64_t)r, (uint32_t)b.ctl[1], b.q);
+  const uint32_t sweep = (uint32_t)b.ctl[1];
+  for (uint32_t k = lane; k < n; k += 32) {
+    const uint32_t l = b.olist[(uint64_t)t * R::kOpenCap + k];
+    const LabelT r = find_global(T, (LabelT)global_index(lat, x0, y0, l), b.err);
+    b.nso[(uint64_t)t * R::kOpenCap + k] = (uint8_t)cluster_state(b.seed, (uint64_t)r, sweep, b.q);
+  }
 }
 
 // ================================================================== k_recolor
@@ -955,6 +957,26 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const __grid_constant__ Sr
   LabelT* T = reinterpret_cast<LabelT*>(b.T);
   const uint8_t* nso = b.nso + (uint64_t)t * R::kOpenCap;
   const uint16_t* ol = b.olist + (uint64_t)t * R::kOpenCap;
+  if (!kRoots && (L & 7u) == 0) {
+    // rows of 8-site groups: a thread reads 8 codes (16 B), writes 8 spins
+    const int lx = 8 * (tid & 15);
+    for (int ly = tid >> 4; ly < h; ly += kThreads / 16) {
+      if (lx < w) {
+        const uint64_t gi = (y0 + ly) * L + x0 + lx;
+        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(b.code + gi));
+        const uint32_t cw[4] = {v.x, v.y, v.z, v.w};
+        uint32_t s2[2] = {0u, 0u};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const uint32_t c = (cw[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
+          const uint32_t st = (c & kClosed) ? (c & 0xFFu) : nso[c];
+          s2[k >> 2] |= st << (8 * (k & 3));
+        }
+        *reinterpret_cast<uint2*>(b.spin + gi) = make_uint2(s2[0], s2[1]);
+      }
+    }
+    return;
+  }
   const int lx0 = 4 * lane;
 #pragma unroll
   for (int rr = 0; rr < kRpw; ++rr) {
@@ -1029,6 +1051,34 @@ static __global__ void __launch_bounds__(256) k_measure(const uint8_t* s, Lattic
   const uint64_t groups = (L + 3) >> 2;
   const uint32_t qs = q <= 8 ? q - 1 : 0;
   uint32_t e = 0, cnt[7] = {0, 0, 0, 0, 0, 0, 0}, nsites = 0;
+  if ((L & 15u) == 0) {
+    // rows over blocks, 16-site groups of a row over threads (16 B loads)
+    const uint64_t g16 = L >> 4;
+    for (uint64_t y = blockIdx.x; y < L; y += gridDim.x) {
+      const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
+      for (uint64_t gx = threadIdx.x; gx < g16; gx += blockDim.x) {
+        const uint64_t x = gx * 16;
+        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(s + y * L + x));
+        const uint4 d = *reinterpret_cast<const uint4*>(s + yd * L + x);
+        const uint32_t nx = *reinterpret_cast<const uint32_t*>(s + y * L + ((x + 16 == L) ? 0 : x + 16));
+        const uint32_t w4[5] = {v.x, v.y, v.z, v.w, nx};
+        const uint32_t d4[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t r = __funnelshift_r(w4[k], w4[k + 1], 8);
+          e += __popc(zero_bytes4(w4[k] ^ r)) + __popc(zero_bytes4(w4[k] ^ d4[k]));
+          if (qs) {
+#pragma unroll
+            for (uint32_t st = 0; st < 7; ++st)
+              if (st < qs) cnt[st] += __popc(zero_bytes4(w4[k] ^ (st * 0x01010101u)));
+          } else {
+            for (int j = 0; j < 4; ++j) atomicAdd(&hist[1 + ((w4[k] >> (8 * j)) & 0xFFu)], 1u);
+          }
+        }
+        nsites += 16;
+      }
+    }
+  } else
   // rows over blocks, 4-site groups of a row over threads
   for (uint64_t y = blockIdx.x; y < L; y += gridDim.x) {
     const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
