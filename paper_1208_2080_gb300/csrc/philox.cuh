@@ -39,6 +39,27 @@ __device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32
   return Words4{c0, c1, c2, c3};
 }
 
+// Same function with the ten round keys given (rk[2r], rk[2r+1] = key of
+// round r); when rk lives in the kernel's parameter space the keys are
+// instruction operands and the per-round key additions disappear.
+__device__ __forceinline__ Words4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                   const uint32_t (&rk)[20]) {
+  constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)kMul0 * c0, p1 = (uint64_t)kMul1 * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c1 ^ rk[2 * r];
+    const uint32_t n2 = hi0 ^ c3 ^ rk[2 * r + 1];
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return Words4{c0, c1, c2, c3};
+}
+
 // Stream domains (fourth counter word).
 enum : uint32_t { kDomBond = 0, kDomSpin = 1, kDomInit = 2 };
 
@@ -46,6 +67,11 @@ __device__ __forceinline__ Words4 stream4(uint64_t seed, uint64_t idx, uint32_t 
                                           uint32_t dom) {
   return philox4x32_10((uint32_t)idx, (uint32_t)(idx >> 32), sweep, dom, (uint32_t)seed,
                        (uint32_t)(seed >> 32));
+}
+
+__device__ __forceinline__ Words4 stream4_rk(const uint32_t (&rk)[20], uint64_t idx, uint32_t sweep,
+                                             uint32_t dom) {
+  return philox4x32_10_rk((uint32_t)idx, (uint32_t)(idx >> 32), sweep, dom, rk);
 }
 
 // floor(w * q / 2^32): the state a 32-bit word picks.

@@ -344,6 +344,7 @@ int sw_create_ex(const sw_params* prm, sw_sim** out) {
     return SW_ERR_NOMEM;
   }
   b.seed = prm->seed;
+  set_round_keys(b);
   b.thr = s->thr;
   b.q = s->q;
   b.ring_cap = ring;

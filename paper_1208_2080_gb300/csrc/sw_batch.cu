@@ -231,6 +231,7 @@ int sw_batch_create_ex(const sw_batch_params* p, sw_batch** out) {
     bb.bonds = nullptr;
     bb.err = b->err;
     bb.seed = p->seed[r];
+    set_round_keys(bb);
     bb.thr = bond_threshold(p->T[r]);
     bb.q = p->q[r];
     bb.ring_cap = b->ring;

@@ -118,7 +118,19 @@ struct Bufs {
   uint32_t thr, q;
   uint32_t ring_cap;
   uint32_t measure;           // 1: k_label_tile accumulates observables of its input
+  uint32_t rk[20];            // Philox round keys of `seed` (see set_round_keys)
 };
+
+// The ten Philox round keys of a seed: (lo, hi) + r * (Weyl constants).
+__host__ __device__ inline void set_round_keys(Bufs& b) {
+  uint32_t k0 = (uint32_t)b.seed, k1 = (uint32_t)(b.seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    b.rk[2 * r] = k0;
+    b.rk[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
 
 // A replica of the batched runner: its buffers, geometry and first tile in
 // the concatenated tile list.
@@ -562,14 +574,14 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         if ((eqr | eqd) != 0u) {
           const uint64_t i0 = (y0 + ly) * L + x0 + lx0;
           const uint64_t pa = i0 >> 1;
-          const Words4 A = stream4(b.seed, pa, sweep, kDomBond);
-          const Words4 B = stream4(b.seed, pa + 1, sweep, kDomBond);
+          const Words4 A = stream4_rk(b.rk, pa, sweep, kDomBond);
+          const Words4 B = stream4_rk(b.rk, pa + 1, sweep, kDomBond);
           uint32_t wr[4], wd[4];
           if ((i0 & 1u) == 0u) {
             wr[0] = A.x; wd[0] = A.y; wr[1] = A.z; wd[1] = A.w;
             wr[2] = B.x; wd[2] = B.y; wr[3] = B.z; wd[3] = B.w;
           } else {
-            const Words4 C = stream4(b.seed, pa + 2, sweep, kDomBond);
+            const Words4 C = stream4_rk(b.rk, pa + 2, sweep, kDomBond);
             wr[0] = A.z; wd[0] = A.w; wr[1] = B.x; wd[1] = B.y;
             wr[2] = B.z; wd[2] = B.w; wr[3] = C.x; wd[3] = C.y;
           }
@@ -763,7 +775,8 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
       if (!kRoots) {
         for (uint32_t i = lane; i < nclosed; i += 32) {
           const uint32_t j = wl[i];
-          const uint32_t stt = cluster_state(b.seed, global_index(lat, x0, y0, j), sweep, q_states);
+          const uint32_t stt =
+              pick_state(stream4_rk(b.rk, global_index(lat, x0, y0, j), sweep, kDomSpin).x, q_states);
           P[j] = j | (stt << 16);
         }
       }
@@ -932,7 +945,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_resolve(const __grid_constant
   for (uint32_t k = lane; k < n; k += 32) {
     const uint32_t l = b.olist[(uint64_t)t * R::kOpenCap + k];
     const LabelT r = find_global(T, (LabelT)global_index(lat, x0, y0, l), b.err);
-    b.nso[(uint64_t)t * R::kOpenCap + k] = (uint8_t)cluster_state(b.seed, (uint64_t)r, sweep, b.q);
+    b.nso[(uint64_t)t * R::kOpenCap + k] =
+        (uint8_t)pick_state(stream4_rk(b.rk, (uint64_t)r, sweep, kDomSpin).x, b.q);
   }
 }
 
