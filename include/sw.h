@@ -270,6 +270,23 @@ int sw_label_bonds_le(uint64_t L, const uint8_t *bonds, void *roots,
                       uint32_t label_bits, uint32_t max_iter,
                       uint32_t *iterations, void *stream);
 
+/* The paper's multi-GPU labelling (Sec. 3), emulated on one GPU for
+ * comparison: the lattice is split into (L/sub)^2 sub-lattices of sub x sub
+ * sites (sub must divide L).  Stage 1 labels each sub-lattice by label
+ * equivalence, ignoring bonds that leave it; stage 2 iterates scanning and
+ * analysis on a label_total table over the boundary layers only (the
+ * bonds crossing sub-lattice boundaries); finally every site adopts
+ * label_total of its stage-1 label.  Same inputs and result as
+ * sw_label_bonds (bit-identical roots).  iterations (may be NULL) receives
+ * {stage-1 rounds, stage-2 rounds}; stage_ms (may be NULL) receives the
+ * CUDA-event times in ms of {stage 1, stage 2, final update}, each round's
+ * host convergence check included.  A scratch table of N labels is
+ * allocated through the library's allocator for label_total (SW_ERR_NOMEM
+ * if that fails).  Synchronises `stream`. */
+int sw_label_bonds_2stage(uint64_t L, uint64_t sub, const uint8_t *bonds,
+                          void *roots, uint32_t label_bits,
+                          uint32_t *iterations, float *stage_ms, void *stream);
+
 /* Step (2) alone, like sw_label_bonds, for callers that cannot allocate
  * device memory: a program whose GPU memory belongs to a framework pool it
  * cannot borrow from, or one that must not call cudaMalloc/cudaFree once

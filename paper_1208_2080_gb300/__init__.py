@@ -5,7 +5,7 @@ this package is its thin Python binding.  See ``Sim`` (one lattice),
 ``label_bonds`` (labelling step alone) and ``threshold``.
 """
 from ._binding import (  # noqa: F401
-    EXPORTS, LIB_PATH, Batch, Mlp, Sim, SwError, check, label_bonds, label_bonds_le, label_bonds_static, lib, pack_bonds, strerror, threshold,
+    EXPORTS, LIB_PATH, Batch, Mlp, Sim, SwError, check, label_bonds, label_bonds_2stage, label_bonds_le, label_bonds_static, lib, pack_bonds, strerror, threshold,
     unpack_bonds, use_cuda_malloc, use_torch_allocator,
 )
 

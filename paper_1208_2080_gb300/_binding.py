@@ -37,6 +37,7 @@ EXPORTS = [
     "sw_batch_profile", "sw_batch_profile_read", "sw_batch_last_error", "sw_label_bonds_static",
     "sw_mlp_create", "sw_mlp_destroy", "sw_mlp_bind_stream", "sw_mlp_forward", "sw_mlp_gradients",
     "sw_mlp_train_step", "sw_mlp_get_params", "sw_mlp_set_params", "sw_label_bonds_le",
+    "sw_label_bonds_2stage",
 ]
 
 
@@ -146,6 +147,8 @@ def lib():
         "sw_mlp_get_params": (i32, [vp, vp, vp]),
         "sw_mlp_set_params": (i32, [vp, vp]),
         "sw_label_bonds_le": (i32, [u64, vp, vp, u32, u32, ctypes.POINTER(ctypes.c_uint32), vp]),
+        "sw_label_bonds_2stage": (i32, [u64, u64, vp, vp, u32, ctypes.POINTER(ctypes.c_uint32),
+                                        ctypes.POINTER(ctypes.c_float), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -495,6 +498,21 @@ class Mlp:
 
 
 LABEL_STATIC_MAX_L = 1024
+
+
+def label_bonds_2stage(L, sub, bonds_dev, roots_dev, label_bits=32, stream=None, timings=False):
+    """The paper's two-stage (multi-GPU) labelling emulated with (L/sub)^2
+    sub-lattices; returns (stage-1 rounds, stage-2 rounds), plus the stage
+    times in ms (stage 1, stage 2, final update) if `timings`."""
+    it = (ctypes.c_uint32 * 2)()
+    ms = (ctypes.c_float * 3)()
+    check(lib().sw_label_bonds_2stage(int(L), int(sub), ctypes.c_void_p(bonds_dev.data_ptr()),
+                                      ctypes.c_void_p(roots_dev.data_ptr()), int(label_bits), it,
+                                      ms if timings else None, _stream_handle(stream)),
+          "sw_label_bonds_2stage")
+    if timings:
+        return int(it[0]), int(it[1]), tuple(float(x) for x in ms)
+    return int(it[0]), int(it[1])
 
 
 def label_bonds_le(L, bonds_dev, roots_dev, label_bits=32, max_iter=0, stream=None):

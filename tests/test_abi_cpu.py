@@ -57,3 +57,12 @@ def test_bond_packing_roundtrip():
     for L in [2, 3, 5, 8, 13]:
         b = rng.integers(0, 4, size=(L, L)).astype(np.uint8)
         assert np.array_equal(sw.unpack_bonds(sw.pack_bonds(b), L), b)
+
+
+def test_two_stage_labeller_rejects_bad_sub_lattices_before_device_work():
+    import ctypes
+    f = sw.lib().sw_label_bonds_2stage
+    p = ctypes.c_void_p(16)  # never dereferenced: every call below fails argument checks
+    for L, sub, bits in [(12, 5, 32), (12, 1, 32), (12, 24, 32), (1, 1, 32), (12, 6, 16),
+                         (1 << 21, 1 << 20, 64), (1 << 17, 1 << 16, 32)]:
+        assert f(L, sub, p, p, bits, None, None, None) == -1, (L, sub, bits)
