@@ -8,6 +8,10 @@ It wraps the plain C oracle in ``sw_oracle.c`` (conventions in
 Every function follows Sec. 2 of Komura & Okabe (Eq. 1 and the three SW
 steps); measurement follows Sec. 4 (Table 1, "update + measurement").
 
+The ``xy_*`` functions wrap ``xy_oracle.c``: the embedded-cluster sweep of
+the XY model with M angles that Sec. 5 names as the extension (Wolff's
+embedding), pinned in tests/test_oracle_xy.py.
+
 Pins (tests/test_oracle_*.py): Philox known-answer vectors and an
 independent Philox implementation, BFS labelling, exact SW transition
 matrices (stationarity + detailed balance), brute-force and transfer-matrix
@@ -54,6 +58,21 @@ def lib():
                               ctypes.c_uint64, u8p, ctypes.c_uint32, ctypes.c_uint32,
                               u64p, u64p]
         L.orc_run.restype = ctypes.c_int
+        L.orc_xy_axis.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
+        L.orc_xy_axis.restype = ctypes.c_uint32
+        L.orc_xy_thresholds.argtypes = [ctypes.c_uint32, ctypes.c_double, u32p]
+        L.orc_xy_thresholds.restype = None
+        L.orc_xy_bonds.argtypes = [ctypes.c_uint64, ctypes.c_uint32, u8p, u32p, ctypes.c_uint32,
+                                   ctypes.c_uint64, ctypes.c_uint32, u8p]
+        L.orc_xy_bonds.restype = None
+        L.orc_xy_flip.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                                  ctypes.c_uint32, u32p, u8p]
+        L.orc_xy_flip.restype = None
+        L.orc_xy_measure.argtypes = [ctypes.c_uint64, ctypes.c_uint32, u8p, u64p, u64p]
+        L.orc_xy_measure.restype = None
+        L.orc_xy_run.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64,
+                                 u8p, ctypes.c_uint32, ctypes.c_uint32, u64p, u64p]
+        L.orc_xy_run.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -156,3 +175,89 @@ def tc(q):
     """Critical temperature of the 2D q-state Potts model, T_c = 1/ln(1+sqrt q)
     (Sec. 4 quotes T_c = 1.1346 for q = 2)."""
     return 1.0 / np.log1p(np.sqrt(q))
+
+
+# ---------------------------------------------------------------- XY model
+# Embedded-cluster SW sweep of the 2D XY model with M angles (Sec. 5 of the
+# paper; Wolff's embedding).  Conventions in xy_oracle.h.
+
+def xy_axis(seed, sweep, M):
+    """Axis index j of a sweep: r at angle pi j/M - pi/2, reflection k -> (j-k) mod M."""
+    return int(lib().orc_xy_axis(int(seed), int(sweep), int(M)))
+
+
+def xy_thresholds(M, T):
+    """(M//2+1, M//2+1) table floor((1 - exp(-2 sin(pi c/M) sin(pi d/M)/T)) 2^32)."""
+    H = M // 2
+    tt = np.zeros((H + 1) * (H + 1), dtype=np.uint32)
+    lib().orc_xy_thresholds(int(M), float(T), _p(tt, ctypes.c_uint32))
+    return tt.reshape(H + 1, H + 1)
+
+
+def xy_bonds(spins, M, T, seed, sweep, j=None):
+    """Step (1) of the embedded sweep: bond bits (bit0 right, bit1 down)."""
+    s = np.ascontiguousarray(spins, dtype=np.uint8)
+    L = s.shape[0]
+    tt = np.ascontiguousarray(xy_thresholds(M, T).reshape(-1))
+    jj = xy_axis(seed, sweep, M) if j is None else int(j)
+    b = np.zeros(L * L, dtype=np.uint8)
+    lib().orc_xy_bonds(L, M, _p(s, ctypes.c_uint8), _p(tt, ctypes.c_uint32), jj, seed, sweep,
+                       _p(b, ctypes.c_uint8))
+    return b.reshape(L, L)
+
+
+def xy_flip(spins, root, M, seed, sweep, j=None):
+    """Step (3): clusters reflected k -> (j-k) mod M by their root's coin."""
+    s = np.array(spins, dtype=np.uint8, copy=True, order="C")
+    r = np.ascontiguousarray(root, dtype=np.uint32)
+    L = s.shape[0]
+    jj = xy_axis(seed, sweep, M) if j is None else int(j)
+    lib().orc_xy_flip(L, M, jj, seed, sweep, _p(r, ctypes.c_uint32), _p(s, ctypes.c_uint8))
+    return s
+
+
+def xy_measure(spins, M):
+    """(D[0..M//2], n[0..M-1]) of a configuration."""
+    s = np.ascontiguousarray(spins, dtype=np.uint8)
+    L = s.shape[0]
+    D = np.zeros(M // 2 + 1, dtype=np.uint64)
+    n = np.zeros(M, dtype=np.uint64)
+    lib().orc_xy_measure(L, M, _p(s, ctypes.c_uint8), _p(D, ctypes.c_uint64),
+                         _p(n, ctypes.c_uint64))
+    return D, n
+
+
+def xy_init(L, M, seed):
+    """Initial angles from the init stream (the Potts init with q = M)."""
+    return init_spins(L, M, seed)
+
+
+def xy_run(L, M, T, seed, nsweeps, spins=None, sweep0=0, series=True):
+    """Run nsweeps embedded-cluster sweeps.  Returns (spins, D_series,
+    n_series), entry k being the configuration after sweep sweep0+k."""
+    s = xy_init(L, M, seed).reshape(-1).copy() if spins is None else \
+        np.array(spins, dtype=np.uint8, copy=True).reshape(-1)
+    H = M // 2
+    D = np.zeros((max(nsweeps, 1), H + 1), dtype=np.uint64) if series else None
+    n = np.zeros((max(nsweeps, 1), M), dtype=np.uint64) if series else None
+    rc = lib().orc_xy_run(L, M, float(T), seed, _p(s, ctypes.c_uint8), sweep0, nsweeps,
+                          _p(D, ctypes.c_uint64) if series else None,
+                          _p(n, ctypes.c_uint64) if series else None)
+    if rc != 0:
+        raise ValueError(f"orc_xy_run failed ({rc})")
+    if series:
+        return s.reshape(L, L), D[:nsweeps], n[:nsweeps]
+    return s.reshape(L, L), None, None
+
+
+def xy_energy(D, M):
+    """E = -sum_d D[d] cos(2 pi d / M) (J = 1), per configuration."""
+    D = np.asarray(D, dtype=np.float64)
+    return -(D * np.cos(2 * np.pi * np.arange(M // 2 + 1) / M)).sum(-1)
+
+
+def xy_magnetisation(n, M):
+    """(m_x, m_y) = sum_k n[k] (cos, sin)(2 pi k / M), per configuration."""
+    n = np.asarray(n, dtype=np.float64)
+    a = 2 * np.pi * np.arange(M) / M
+    return (n * np.cos(a)).sum(-1), (n * np.sin(a)).sum(-1)

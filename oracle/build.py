@@ -8,18 +8,19 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "sw_oracle.c")
+SRCS = [os.path.join(HERE, f) for f in ("sw_oracle.c", "xy_oracle.c")]
+HDRS = [os.path.join(HERE, f) for f in ("sw_oracle.h", "xy_oracle.h")]
 LIB = os.path.join(HERE, "liboracle_sw.so")
 
 
 def build(force: bool = False) -> str:
-    """Compile sw_oracle.c into liboracle_sw.so next to it; return the path."""
+    """Compile the oracle's C files into liboracle_sw.so next to them; return
+    the path."""
     if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= max(os.path.getmtime(SRC),
-                                             os.path.getmtime(os.path.join(HERE, "sw_oracle.h")))):
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(f) for f in SRCS + HDRS)):
         return LIB
     cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-Wall", "-Wextra",
-           "-fno-fast-math", "-o", LIB + ".tmp", SRC, "-lm"]
+           "-fno-fast-math", "-o", LIB + ".tmp"] + SRCS + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB

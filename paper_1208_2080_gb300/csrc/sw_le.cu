@@ -139,11 +139,11 @@ __global__ void __launch_bounds__(kThreads) k_2s_scan_local(const uint8_t* __res
   bool any = false;
   for (uint64_t y = blockIdx.y; y < L; y += gridDim.y) {
     const uint64_t yu = y ? y - 1 : L - 1, yd = (y + 1 == L) ? 0 : y + 1;
-    const uint64_t ys = y % S;
+    const uint32_t ys = (uint32_t)y % (uint32_t)S;  // L, S <= 2^20: 32-bit remainders
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < L;
          x += (uint64_t)gridDim.x * blockDim.x) {
       const uint64_t i = y * L + x;
-      const uint64_t xs = x % S;
+      const uint32_t xs = (uint32_t)x % (uint32_t)S;
       const uint64_t xl = x ? x - 1 : L - 1, xr = (x + 1 == L) ? 0 : x + 1;
       const LabelT li = label[i];
       LabelT m = li;

@@ -130,3 +130,80 @@ def sw_transition(L, q, p, label_fn):
         w = p ** k * (1 - p) ** (sat - k) / q ** nc
         P[np.ix_(ids, ids)] += w[:, None]
     return P, E
+
+
+def xy_reflect(k, M, j):
+    """Angle index of spin k reflected across the line perpendicular to the
+    embedding vector r at angle pi j / M - pi / 2, computed with vectors:
+    s' = s - 2 (s . r) r (Wolff's embedding step)."""
+    th = 2 * np.pi * k / M
+    ph = np.pi * j / M - np.pi / 2
+    s = np.array([np.cos(th), np.sin(th)])
+    r = np.array([np.cos(ph), np.sin(ph)])
+    t = s - 2 * (s @ r) * r
+    a = np.arctan2(t[1], t[0]) * M / (2 * np.pi)
+    kk = int(np.rint(a)) % M
+    assert abs(a - np.rint(a)) < 1e-9, "reflection leaves the angle set"
+    return kk
+
+
+def xy_sigma(k, M, j):
+    """s . r for spin k and the embedding vector of axis index j."""
+    return float(np.cos(2 * np.pi * k / M - (np.pi * j / M - np.pi / 2)))
+
+
+def xy_energy_all(L, M):
+    """All M^(L*L) configurations and their energies H = -sum cos(theta_i -
+    theta_j) over the 2N right/down bonds of the periodic L x L lattice."""
+    N = L * L
+    states = np.array(list(itertools.product(range(M), repeat=N)), dtype=np.int16)
+    r_idx, d_idx = neighbours(L)
+    ang = 2 * np.pi * states / M
+    H = -(np.cos(ang - ang[:, r_idx]).sum(1) + np.cos(ang - ang[:, d_idx]).sum(1))
+    return states, H
+
+
+def xy_transition(L, M, T, label_fn):
+    """Exact transition matrix of one embedded-cluster SW sweep (Wolff's
+    embedding, every cluster reflected with probability 1/2) of the M-angle
+    XY model on the L x L torus, built from vector geometry: axis index j
+    uniform in 0..M-1; a bond is eligible iff sigma_i sigma_j > 0 and active
+    with probability 1 - exp(-2 sigma_i sigma_j / T)."""
+    N = L * L
+    states, H = xy_energy_all(L, M)
+    S = len(states)
+    r_idx, d_idx = neighbours(L)
+    powers = M ** np.arange(N - 1, -1, -1)
+    refl = np.array([[xy_reflect(k, M, j) for k in range(M)] for j in range(M)])
+    P = np.zeros((S, S))
+    for si in range(S):
+        s = states[si]
+        for j in range(M):
+            sig = np.array([xy_sigma(int(k), M, j) for k in s])
+            sig[np.abs(sig) < 1e-12] = 0.0
+            bonds = []  # (site, dir, p)
+            for i in range(N):
+                for d, nb in ((0, r_idx[i]), (1, d_idx[i])):
+                    prod = sig[i] * sig[nb]
+                    if prod > 0:
+                        bonds.append((i, d, -np.expm1(-2 * prod / T)))
+            nbd = len(bonds)
+            for mask in range(1 << nbd):
+                w = 1.0 / M
+                b = np.zeros(N, dtype=np.uint8)
+                for t, (i, d, p) in enumerate(bonds):
+                    if (mask >> t) & 1:
+                        w *= p
+                        b[i] |= RIGHT if d == 0 else DOWN
+                    else:
+                        w *= 1 - p
+                if w == 0.0:
+                    continue
+                roots = np.asarray(label_fn(b.reshape(L, L))).ravel()
+                uniq, cl = np.unique(roots, return_inverse=True)
+                nc = len(uniq)
+                for fm in range(1 << nc):
+                    flip = np.array([(fm >> c) & 1 for c in range(nc)])[cl]
+                    s2 = np.where(flip == 1, refl[j][s], s)
+                    P[si, int(s2 @ powers)] += w / (1 << nc)
+    return P, H
