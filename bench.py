@@ -42,6 +42,12 @@ PAPER_UPDATE_MEASURE = 33.85  # Table 1, L=65536, 256x Tesla M2050, update + mea
 ALG_BYTES_PER_SITE = {"k_label_tile": 3.0, "k_merge+k_resolve": 0.0, "k_recolor": 3.0}
 PHASES = ["k_label_tile", "k_merge+k_resolve", "k_recolor"]
 LAUNCHES_PER_SWEEP = 4  # k_label_tile, k_merge, k_resolve, k_recolor
+# XY model (embedded clusters, M angles): the labeller reads the angle and
+# writes the code; the reflection reads code and angle and writes the
+# angle; the measurement reads the angle (halo rows come from L2).
+XY_PHASES = ["k_label_tile<XY>", "k_merge+k_resolve", "k_recolor<XY>", "k_xy_measure"]
+XY_ALG_BYTES_PER_SITE = {"k_label_tile<XY>": 3.0, "k_merge+k_resolve": 0.0, "k_recolor<XY>": 4.0,
+                         "k_xy_measure": 1.0}
 THROTTLE = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
 
@@ -313,6 +319,14 @@ def run_ours(args, rank, world):
         torch.cuda.empty_cache()
         batched = run_batched(args, sw, torch)
 
+    xy = None
+    if args.xy_sweeps > 0:
+        if sim is not None:
+            sim.close()
+            sim = None
+        torch.cuda.empty_cache()
+        xy = run_xy(args, sw, torch)
+
     if rank != 0:
         return 0
     peak, peak_kind = _peaks()
@@ -352,6 +366,7 @@ def run_ours(args, rank, world):
         if upd is not None else None,
         "observables_last": {"config": cfg, "E_sat": E, "n": [int(x) for x in n]},
         "batched": batched,
+        "xy": xy,
     }
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
@@ -359,6 +374,47 @@ def run_ours(args, rank, world):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_xy(args, sw, torch):
+    """The XY model's embedded-cluster sweep (M angles, T = T_KT, all-zero
+    start, measurement after every sweep): spin updates/ns over timed sweeps
+    and the per-phase roofline of its kernels."""
+    import numpy as np
+    L, M = args.xy_L, args.xy_M
+    N = L * L
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = _peaks()
+    with sw.XY(L, M, sw.T_KT, 9, init="zero") as x:
+        x.sweep(args.xy_warmup)
+        x.sync()
+        x.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x.sweep(args.xy_sweeps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        phase_ms, phase_n = x.profile_read()
+        D, n = x.series(x.sweep_count, 1)
+        x.sync()
+    assert int(D.sum()) == 2 * N and int(n.sum()) == N, "XY observables out of range"
+    avg = [m / max(c, 1) for m, c in zip(phase_ms, phase_n)]
+    phases = {}
+    for k, name in enumerate(XY_PHASES):
+        alg = XY_ALG_BYTES_PER_SITE[name] * N
+        gbs = alg / (avg[k] * 1e-3) / 1e9 if avg[k] > 0 else None
+        phases[name] = {"ms": avg[k], "alg_bytes": alg, "GB/s": gbs,
+                        "frac": gbs / peak if gbs else None}
+    dom = max(range(4), key=lambda k: avg[k])
+    return {"workload": f"XY model, M={M} angles, L={L}, T=T_KT={sw.T_KT:.5f}, all-zero start, "
+                        f"sweeps {args.xy_warmup}..{args.xy_warmup + args.xy_sweeps - 1}",
+            "metric": "XY embedded-cluster spin updates/ns (update + measurement)",
+            "value": N * args.xy_sweeps / (ms * 1e6), "unit": UNIT, "steps": args.xy_sweeps,
+            "ms_per_sweep": ms / args.xy_sweeps, "gpu_launches": 6 * args.xy_sweeps,
+            "phases": phases, "dominant": XY_PHASES[dom], "peak": peak, "peak_kind": peak_kind,
+            "energy_per_site_last": float(-(D[0] * np.cos(2 * np.pi * np.arange(M // 2 + 1) / M)).sum()
+                                          / N)}
 
 
 def run_batched(args, sw, torch):
@@ -427,6 +483,10 @@ def main():
     ap.add_argument("--batch-R", type=int, default=512, help="replicas in the batched measurement")
     ap.add_argument("--batch-sweeps", type=int, default=40, help="0 skips the batched measurement")
     ap.add_argument("--plain-sweeps", type=int, default=10)
+    ap.add_argument("--xy-sweeps", type=int, default=20, help="0 skips the XY-model measurement")
+    ap.add_argument("--xy-warmup", type=int, default=5)
+    ap.add_argument("--xy-L", type=int, default=65536)
+    ap.add_argument("--xy-M", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

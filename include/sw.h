@@ -308,6 +308,68 @@ int sw_label_bonds_static(uint64_t L, const uint8_t *bonds, uint32_t *roots,
                           uint32_t tile_h, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * XY model, embedded-cluster sweep (Sec. 5: the extension of the sweep to
+ * the classical XY model through Wolff's embedded clusters), with M equally
+ * spaced angles (spin k in 0..M-1 is the angle 2 pi k / M, one byte; M in
+ * 2..256, M = 256 standing in for continuous angles).  H = -sum cos(theta_i
+ * - theta_j), J = 1.  One sweep:
+ *   (0) embedding axis r at angle pi j / M - pi / 2, j = floor(w M / 2^32)
+ *       with w word 0 of Philox counter (0, 0, sweep, 3);
+ *   (1) the bond (i, k) is active iff sigma_i sigma_k > 0 (sigma = s . r)
+ *       and u < tt[c_i][c_k], u the Potts sweep's bond word, c the fold
+ *       index of |sigma| = sin(pi c / M) and tt the sw_xy_thresholds table;
+ *   (2) clusters labelled as in the Potts sweep (root = smallest index);
+ *   (3) each cluster reflected, k -> (j - k) mod M, iff its coin
+ *       floor(w 2 / 2^32) is 1, w the Potts state word of its root.
+ * Measurement of a configuration: D[d], d in 0..M/2, bonds (right and down,
+ * 2N in all) with angle difference +-d mod M, and n[k], sites at angle k;
+ * E = -sum_d D[d] cos(2 pi d / M).
+ * ------------------------------------------------------------------------- */
+typedef struct sw_xy sw_xy;
+typedef struct {
+  uint64_t L;          /* linear size, 2 .. 2^20 */
+  uint32_t M;          /* angles, 2 .. 256 */
+  uint32_t label_bits; /* 0 = auto (32 up to L = 32768, else 64), 32, 64 */
+  double T;            /* temperature > 0 */
+  uint64_t seed;       /* Philox key */
+  uint32_t tile_h;     /* 0 = auto, 16, 32, 64 */
+  uint32_t ring;       /* configurations whose observables are kept (0 = 1024) */
+  uint32_t init;       /* SW_INIT_RANDOM (angles from the init stream) or SW_INIT_ZERO */
+  uint32_t measure;    /* 0: measure after every sweep; 2: only on request */
+  uint32_t reserved[4];
+} sw_xy_params;
+/* Bond thresholds floor((1 - exp(-2 sin(pi c/M) sin(pi d/M) / T)) 2^32),
+ * clamped to 2^32 - 1, into tt[c * (M/2+1) + d] (host array of
+ * (M/2+1)^2 entries; M/2 rounded down).  Host only. */
+int sw_xy_thresholds(uint32_t M, double T, uint32_t *tt);
+int sw_xy_create(const sw_xy_params *prm, sw_xy **out);
+void sw_xy_destroy(sw_xy *xy);
+int sw_xy_bind_stream(sw_xy *xy, void *stream);
+/* n sweeps (asynchronous; with measurement on, five kernels per sweep:
+ * the four of the Potts sweep in their XY form and the measurement). */
+int sw_xy_sweep(sw_xy *xy, uint64_t n);
+int sw_xy_sync(sw_xy *xy);
+/* Observables of configurations first .. first+count-1 (configuration c is
+ * the one after c sweeps): D (count x (M/2+1)) and n (count x M) host
+ * arrays, either may be NULL.  SW_ERR_RANGE outside the ring window, before
+ * the last sw_xy_set_spins, or (measurement off) for anything but the
+ * current configuration.  Synchronises the stream. */
+int sw_xy_series(sw_xy *xy, uint64_t first, uint64_t count, uint64_t *D,
+                 uint64_t *n);
+/* Copy the N = L*L angles out / in (host or device buffer).  set_spins
+ * validates on the device: an angle >= M gives SW_ERR_INVAL and sweeps
+ * return SW_ERR_STATE until a valid configuration is set. */
+int sw_xy_spins(sw_xy *xy, uint8_t *dst, uint64_t n, int dst_on_device);
+int sw_xy_set_spins(sw_xy *xy, const uint8_t *src, uint64_t n,
+                    int src_on_device);
+int sw_xy_get_sweep(const sw_xy *xy, uint64_t *sweep);
+/* Per-phase CUDA-event timing of sweeps: phases labelling, merge+resolve,
+ * reflection, measurement (as sw_profile). */
+int sw_xy_profile(sw_xy *xy, int enable);
+int sw_xy_profile_read(sw_xy *xy, double *ms, uint64_t *launches, int nphase);
+int sw_xy_last_error(const sw_xy *xy);
+
+/* ---------------------------------------------------------------------------
  * Surrogate network (not in the paper): a 3 -> 64 -> 64 -> 64 -> 4 tanh MLP
  * with bfloat16 weights and fp32 accumulation that maps (q, log2 L, T/T_c)
  * to standardised observables and only places temperature grids.

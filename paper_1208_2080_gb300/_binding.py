@@ -38,6 +38,9 @@ EXPORTS = [
     "sw_mlp_create", "sw_mlp_destroy", "sw_mlp_bind_stream", "sw_mlp_forward", "sw_mlp_gradients",
     "sw_mlp_train_step", "sw_mlp_get_params", "sw_mlp_set_params", "sw_label_bonds_le",
     "sw_label_bonds_2stage",
+    "sw_xy_thresholds", "sw_xy_create", "sw_xy_destroy", "sw_xy_bind_stream", "sw_xy_sweep",
+    "sw_xy_sync", "sw_xy_series", "sw_xy_spins", "sw_xy_set_spins", "sw_xy_get_sweep",
+    "sw_xy_profile", "sw_xy_profile_read", "sw_xy_last_error",
 ]
 
 
@@ -58,6 +61,13 @@ class sw_params(ctypes.Structure):
                 ("ring", ctypes.c_uint32), ("init", ctypes.c_uint32),
                 ("store_bonds", ctypes.c_uint32), ("measure", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32 * 3)]
+
+
+class sw_xy_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_uint64), ("M", ctypes.c_uint32), ("label_bits", ctypes.c_uint32),
+                ("T", ctypes.c_double), ("seed", ctypes.c_uint64), ("tile_h", ctypes.c_uint32),
+                ("ring", ctypes.c_uint32), ("init", ctypes.c_uint32), ("measure", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 4)]
 
 
 class sw_info_t(ctypes.Structure):
@@ -147,6 +157,19 @@ def lib():
         "sw_mlp_get_params": (i32, [vp, vp, vp]),
         "sw_mlp_set_params": (i32, [vp, vp]),
         "sw_label_bonds_le": (i32, [u64, vp, vp, u32, u32, ctypes.POINTER(ctypes.c_uint32), vp]),
+        "sw_xy_thresholds": (i32, [u32, ctypes.c_double, ctypes.POINTER(ctypes.c_uint32)]),
+        "sw_xy_create": (i32, [ctypes.POINTER(sw_xy_params), ctypes.POINTER(vp)]),
+        "sw_xy_destroy": (None, [vp]),
+        "sw_xy_bind_stream": (i32, [vp, vp]),
+        "sw_xy_sweep": (i32, [vp, u64]),
+        "sw_xy_sync": (i32, [vp]),
+        "sw_xy_series": (i32, [vp, u64, u64, u64p, u64p]),
+        "sw_xy_spins": (i32, [vp, vp, u64, i32]),
+        "sw_xy_set_spins": (i32, [vp, vp, u64, i32]),
+        "sw_xy_get_sweep": (i32, [vp, u64p]),
+        "sw_xy_profile": (i32, [vp, i32]),
+        "sw_xy_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), u64p, i32]),
+        "sw_xy_last_error": (i32, [vp]),
         "sw_label_bonds_2stage": (i32, [u64, u64, vp, vp, u32, ctypes.POINTER(ctypes.c_uint32),
                                         ctypes.POINTER(ctypes.c_float), vp]),
     }
@@ -326,6 +349,120 @@ class Sim:
         ms = (ctypes.c_double * 3)()
         n = (ctypes.c_uint64 * 3)()
         check(lib().sw_profile_read(self._h, ms, n, 3), "sw_profile_read")
+        return list(ms), list(n)
+
+    @property
+    def handle(self):
+        return self._h
+
+
+def xy_thresholds(M, T):
+    """The XY bond threshold table (host computation of the library)."""
+    H = int(M) // 2
+    tt = np.zeros((H + 1) * (H + 1), dtype=np.uint32)
+    check(lib().sw_xy_thresholds(int(M), float(T), tt.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))),
+          "sw_xy_thresholds")
+    return tt.reshape(H + 1, H + 1)
+
+
+class XY:
+    """The XY model with M angles on an L x L lattice, embedded-cluster
+    sweeps (include/sw.h, sw_xy_*)."""
+
+    def __init__(self, L, M, T, seed, *, label_bits=0, tile_h=0, ring=0, init="random",
+                 measure=True, stream=None):
+        if not _allocator_chosen:
+            use_torch_allocator()
+        p = sw_xy_params()
+        p.L, p.M, p.T, p.seed = int(L), int(M), float(T), int(seed)
+        p.label_bits, p.tile_h, p.ring = int(label_bits), int(tile_h), int(ring)
+        p.init = SW_INIT_ZERO if init == "zero" else SW_INIT_RANDOM
+        p.measure = 0 if measure else 2
+        h = ctypes.c_void_p()
+        self._h = None
+        check(lib().sw_xy_create(ctypes.byref(p), ctypes.byref(h)), "sw_xy_create")
+        self._h = h
+        self.L, self.M, self.T, self.seed = int(L), int(M), float(T), int(seed)
+        self.N = self.L * self.L
+        if stream is not False:
+            self.bind_stream(stream)
+
+    def close(self):
+        if self._h is not None:
+            lib().sw_xy_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def bind_stream(self, stream=None):
+        check(lib().sw_xy_bind_stream(self._h, _stream_handle(stream)), "sw_xy_bind_stream")
+
+    def sweep(self, n=1):
+        check(lib().sw_xy_sweep(self._h, int(n)), "sw_xy_sweep")
+
+    def sync(self):
+        check(lib().sw_xy_sync(self._h), "sw_xy_sync")
+
+    def series(self, first, count):
+        """(D, n): count x (M//2+1) and count x M observables of
+        configurations first .. first+count-1."""
+        D = np.zeros((count, self.M // 2 + 1), dtype=np.uint64)
+        n = np.zeros((count, self.M), dtype=np.uint64)
+        check(lib().sw_xy_series(self._h, int(first), int(count),
+                                 D.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                 n.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))), "sw_xy_series")
+        return D, n
+
+    def measure(self):
+        """(D, n, configuration index) of the current configuration."""
+        c = self.sweep_count
+        D, n = self.series(c, 1)
+        return D[0], n[0], c
+
+    def spins(self, out=None):
+        if out is not None:
+            assert out.is_cuda and out.numel() == self.N and out.is_contiguous()
+            check(lib().sw_xy_spins(self._h, ctypes.c_void_p(out.data_ptr()), self.N, 1), "sw_xy_spins")
+            return out
+        a = np.empty(self.N, dtype=np.uint8)
+        check(lib().sw_xy_spins(self._h, a.ctypes.data_as(ctypes.c_void_p), self.N, 0), "sw_xy_spins")
+        return a.reshape(self.L, self.L)
+
+    def set_spins(self, src):
+        if hasattr(src, "is_cuda") and src.is_cuda:
+            assert src.numel() == self.N and src.is_contiguous()
+            check(lib().sw_xy_set_spins(self._h, ctypes.c_void_p(src.data_ptr()), self.N, 1),
+                  "sw_xy_set_spins")
+            return
+        a = np.ascontiguousarray(np.asarray(src, dtype=np.uint8).reshape(-1))
+        check(lib().sw_xy_set_spins(self._h, a.ctypes.data_as(ctypes.c_void_p), self.N, 0),
+              "sw_xy_set_spins")
+
+    @property
+    def sweep_count(self):
+        v = ctypes.c_uint64()
+        check(lib().sw_xy_get_sweep(self._h, ctypes.byref(v)), "sw_xy_get_sweep")
+        return int(v.value)
+
+    def profile(self, enable=True):
+        check(lib().sw_xy_profile(self._h, 1 if enable else 0), "sw_xy_profile")
+
+    def profile_read(self):
+        """(ms[4], launches[4]) per phase: labelling, merge+resolve,
+        reflection, measurement."""
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_uint64 * 4)()
+        check(lib().sw_xy_profile_read(self._h, ms, n, 4), "sw_xy_profile_read")
         return list(ms), list(n)
 
     @property

@@ -61,7 +61,7 @@ __device__ __forceinline__ Words4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uin
 }
 
 // Stream domains (fourth counter word).
-enum : uint32_t { kDomBond = 0, kDomSpin = 1, kDomInit = 2 };
+enum : uint32_t { kDomBond = 0, kDomSpin = 1, kDomInit = 2, kDomAxis = 3 };
 
 __device__ __forceinline__ Words4 stream4(uint64_t seed, uint64_t idx, uint32_t sweep,
                                           uint32_t dom) {

@@ -119,6 +119,9 @@ struct Bufs {
   uint32_t ring_cap;
   uint32_t measure;           // 1: k_label_tile accumulates observables of its input
   uint32_t rk[20];            // Philox round keys of `seed` (see set_round_keys)
+  // XY model (embedded clusters, M angles; q = 2 coins): 0 for Potts
+  uint32_t M;
+  const uint32_t* tt;         // (M/2+1)^2 bond thresholds by |sigma| fold index
 };
 
 // The ten Philox round keys of a seed: (lo, hi) + r * (Weyl constants).
@@ -386,7 +389,7 @@ __device__ __forceinline__ uint32_t byte_mask(uint32_t nib) {
 // moved with one 16-byte shared-memory access (conflict free); unions and
 // compressions are compacted into per-warp task queues so that all lanes
 // stay busy.
-template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src>
+template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY = false>
 __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks)
     k_label_tile(const __grid_constant__ Src src) {
   static_assert(TH % 16 == 0 && kTW * TH <= 32768, "tile shape");
@@ -503,7 +506,7 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     const uint32_t t = g - src.tile0(rep);
     const uint64_t L = lat.L;
     const uint32_t q_states = b.q;
-    const bool measure = !kGiven && b.measure;
+    const bool measure = !kGiven && !kXY && b.measure;
     const uint32_t sweep = kGiven ? 0u : (uint32_t)b.ctl[0];
     const uint32_t qs = q_states <= 4 ? q_states - 1 : 0;  // states counted in registers
     LabelT* T = reinterpret_cast<LabelT*>(b.T);
@@ -525,6 +528,20 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         stage(gn, sp + ((it + 1) & 1u) * S::kSpBuf, true);
         cp_async_commit();
         pre = true;
+      }
+    }
+    if constexpr (kXY) {
+      // projection class of every angle on this sweep's embedding axis
+      // (Wolff's embedding): sign of sigma in bits 8-9 (1 negative,
+      // 2 positive, 0 zero), fold index c of |sigma| = sin(pi c / M) below
+      uint16_t* xcls = reinterpret_cast<uint16_t*>(sobs);
+      const uint32_t M = b.M;
+      const uint32_t jx = pick_state(stream4_rk(b.rk, 0ull, sweep, kDomAxis).x, M);
+      for (uint32_t k = tid; k < M; k += kThreads) {
+        const uint32_t a = (2 * k >= jx) ? 2 * k - jx : 2 * k + 2 * M - jx;  // (2k - j) mod 2M
+        const uint32_t sg = (a == 0 || a == M) ? 0u : (a < M ? 1u : 2u);
+        const uint32_t bm = a >= M ? a - M : a;
+        xcls[k] = (uint16_t)((sg << 8) | (bm < M - bm ? bm : M - bm));
       }
     }
     if (tid == 0) nsites += (uint32_t)(w * h);
@@ -557,9 +574,34 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         const uint32_t sn = *reinterpret_cast<const uint32_t*>(spc + ly * kSpPitch + lx0 + 4);
         const uint32_t sd = *reinterpret_cast<const uint32_t*>(spc + (ly + 1) * kSpPitch + lx0);
         const uint32_t sr = __funnelshift_r(s, sn, 8);
-        const uint32_t eqr = zero_bytes4(s ^ sr) & vm;  // right neighbour has the same state
-        const uint32_t eqd = zero_bytes4(s ^ sd) & vm;  // lower neighbour has the same state
-        if (measure) {
+        uint32_t eqr, eqd;  // bond candidates: equal states (Potts), equal signs of sigma (XY)
+        uint32_t tr[4], td[4];
+        if constexpr (kXY) {
+          const uint16_t* xcls = reinterpret_cast<const uint16_t*>(sobs);
+          const uint32_t H1 = (b.M >> 1) + 1;
+          uint32_t cs[5], cd[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            cs[k] = xcls[(s >> (8 * k)) & 0xFFu];
+            cd[k] = xcls[(sd >> (8 * k)) & 0xFFu];
+          }
+          cs[4] = xcls[sn & 0xFFu];
+          eqr = eqd = 0;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t sg = cs[k] >> 8;
+            eqr |= (sg != 0u && sg == (cs[k + 1] >> 8)) ? (1u << k) : 0u;
+            eqd |= (sg != 0u && sg == (cd[k] >> 8)) ? (1u << k) : 0u;
+            tr[k] = __ldg(b.tt + (cs[k] & 0xFFu) * H1 + (cs[k + 1] & 0xFFu));
+            td[k] = __ldg(b.tt + (cs[k] & 0xFFu) * H1 + (cd[k] & 0xFFu));
+          }
+          eqr &= vm;
+          eqd &= vm;
+        } else {
+          eqr = zero_bytes4(s ^ sr) & vm;  // right neighbour has the same state
+          eqd = zero_bytes4(s ^ sd) & vm;  // lower neighbour has the same state
+        }
+        if (!kXY && measure) {
           e_loc += __popc(eqr) + __popc(eqd);
           if (qs) {
 #pragma unroll
@@ -585,12 +627,20 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
             wr[0] = A.z; wd[0] = A.w; wr[1] = B.x; wd[1] = B.y;
             wr[2] = B.z; wd[2] = B.w; wr[3] = C.x; wd[3] = C.y;
           }
-          const uint32_t thr = b.thr;
           uint32_t ur = 0, ud = 0;  // u < thr per site
+          if constexpr (kXY) {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            ur |= (wr[k] < thr ? 1u : 0u) << k;
-            ud |= (wd[k] < thr ? 1u : 0u) << k;
+            for (int k = 0; k < 4; ++k) {
+              ur |= (wr[k] < tr[k] ? 1u : 0u) << k;
+              ud |= (wd[k] < td[k] ? 1u : 0u) << k;
+            }
+          } else {
+            const uint32_t thr = b.thr;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              ur |= (wr[k] < thr ? 1u : 0u) << k;
+              ud |= (wd[k] < thr ? 1u : 0u) << k;
+            }
           }
           br = eqr & ur;
           bd = eqd & ud;
@@ -954,7 +1004,9 @@ __global__ void __launch_bounds__(kMergeThreads) k_resolve(const __grid_constant
 // Streams codes to spins: closed clusters carry their state in the code,
 // open ones index the tile's resolved open-root states.
 // kRoots: write each site's global root (LabelT) to `roots` instead.
-template <int TH, typename LabelT, bool kRoots, typename Src>
+// kXY: the coin of each cluster (q = 2) says whether its spins are
+// reflected, k -> (j - k) mod M, j the sweep's embedding axis.
+template <int TH, typename LabelT, bool kRoots, typename Src, bool kXY = false>
 __global__ void __launch_bounds__(kThreads) k_recolor(const __grid_constant__ Src src, LabelT* roots) {
   using R = TileRec<TH>;
   constexpr int kRpw = TH / kWarps;
@@ -971,6 +1023,19 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const __grid_constant__ Sr
   LabelT* T = reinterpret_cast<LabelT*>(b.T);
   const uint8_t* nso = b.nso + (uint64_t)t * R::kOpenCap;
   const uint16_t* ol = b.olist + (uint64_t)t * R::kOpenCap;
+  uint32_t jx = 0, Mx = 0;
+  if constexpr (kXY) {
+    __shared__ uint32_t s_axis;
+    if (tid == 0) s_axis = pick_state(stream4_rk(b.rk, 0ull, (uint32_t)b.ctl[1], kDomAxis).x, b.M);
+    __syncthreads();
+    jx = s_axis;
+    Mx = b.M;
+  }
+  // new spin of a site with old spin k whose cluster drew st
+  auto next = [&](uint32_t st, uint32_t k) -> uint32_t {
+    if constexpr (kXY) return st ? (k <= jx ? jx - k : jx + Mx - k) : k;
+    else return st;
+  };
   if (!kRoots && (L & 7u) == 0) {
     // rows of 8-site groups: a thread reads 8 codes (16 B), writes 8 spins
     const int lx = 8 * (tid & 15);
@@ -979,12 +1044,15 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const __grid_constant__ Sr
         const uint64_t gi = (y0 + ly) * L + x0 + lx;
         const uint4 v = __ldcs(reinterpret_cast<const uint4*>(b.code + gi));
         const uint32_t cw[4] = {v.x, v.y, v.z, v.w};
+        uint2 old = make_uint2(0u, 0u);
+        if constexpr (kXY) old = *reinterpret_cast<const uint2*>(b.spin + gi);
+        const uint32_t ow[2] = {old.x, old.y};
         uint32_t s2[2] = {0u, 0u};
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const uint32_t c = (cw[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
           const uint32_t st = (c & kClosed) ? (c & 0xFFu) : nso[c];
-          s2[k >> 2] |= st << (8 * (k & 3));
+          s2[k >> 2] |= next(st, (ow[k >> 2] >> (8 * (k & 3))) & 0xFFu) << (8 * (k & 3));
         }
         *reinterpret_cast<uint2*>(b.spin + gi) = make_uint2(s2[0], s2[1]);
       }
@@ -1018,11 +1086,21 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const __grid_constant__ Sr
           }
         }
       } else {
+        uint32_t ok = 0;  // old spins (XY only)
+        if constexpr (kXY) {
+          if (lat.vec4) {
+            ok = *reinterpret_cast<const uint32_t*>(b.spin + gi);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              if (lx0 + k < w) ok |= (uint32_t)b.spin[gi + k] << (8 * k);
+          }
+        }
         uint32_t s = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const uint32_t v = (c[k] & kClosed) ? (c[k] & 0xFFu) : nso[c[k]];
-          s |= v << (8 * k);
+          s |= next(v, (ok >> (8 * k)) & 0xFFu) << (8 * k);
         }
         if (lat.vec4) {
           *reinterpret_cast<uint32_t*>(b.spin + gi) = s;

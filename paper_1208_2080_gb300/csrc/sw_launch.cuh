@@ -12,9 +12,9 @@ namespace swgb {
 // Sets the kernel's shared-memory attributes and returns how many tile CTAs
 // fit on the GPU at once (done once per instantiation; call it before any
 // stream capture).
-template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src>
+template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY = false>
 cudaError_t configure_label(int* resident_out) {
-  auto kern = k_label_tile<TH, LabelT, kGiven, kRoots, Src>;
+  auto kern = k_label_tile<TH, LabelT, kGiven, kRoots, Src, kXY>;
   const int smem = LabelSmem<TH>::kBytes;
   static int resident = 0;
   if (!resident) {
@@ -35,12 +35,12 @@ cudaError_t configure_label(int* resident_out) {
   return cudaSuccess;
 }
 
-template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src>
+template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY = false>
 cudaError_t launch_label_src(const Src& src, uint32_t ntiles, cudaStream_t st) {
-  auto kern = k_label_tile<TH, LabelT, kGiven, kRoots, Src>;
+  auto kern = k_label_tile<TH, LabelT, kGiven, kRoots, Src, kXY>;
   const int smem = LabelSmem<TH>::kBytes;
   int resident = 0;
-  cudaError_t e = configure_label<TH, LabelT, kGiven, kRoots, Src>(&resident);
+  cudaError_t e = configure_label<TH, LabelT, kGiven, kRoots, Src, kXY>(&resident);
   if (e != cudaSuccess) return e;
   const uint32_t grid = ntiles < (uint32_t)resident ? ntiles : (uint32_t)resident;
   kern<<<grid, TileCta<TH>::kThreads, smem, st>>>(src);
@@ -63,35 +63,37 @@ cudaError_t launch_resolve_src(const Src& src, uint32_t ntiles, cudaStream_t st)
   return cudaGetLastError();
 }
 
-template <int TH, typename LabelT, bool kRoots, typename Src>
+template <int TH, typename LabelT, bool kRoots, typename Src, bool kXY = false>
 cudaError_t launch_recolor_src(const Src& src, uint32_t ntiles, LabelT* roots, cudaStream_t st) {
-  k_recolor<TH, LabelT, kRoots, Src><<<ntiles, kThreads, 0, st>>>(src, roots);
+  k_recolor<TH, LabelT, kRoots, Src, kXY><<<ntiles, kThreads, 0, st>>>(src, roots);
   return cudaGetLastError();
 }
 
 // One full sweep (four launches) of every lattice the source names; `ev`
 // (four events or null) is recorded before, between and after the phases.
-template <int TH, typename LabelT, typename Src>
+// kXY: the embedded-cluster sweep of the XY model (Potts kernels with the
+// XY bond rule and reflections).
+template <int TH, typename LabelT, typename Src, bool kXY = false>
 cudaError_t sweep_src(const Src& src, uint32_t ntiles, cudaStream_t st, cudaEvent_t* ev) {
   cudaError_t e;
   if (ev && (e = cudaEventRecord(ev[0], st))) return e;
-  if ((e = launch_label_src<TH, LabelT, false, false>(src, ntiles, st))) return e;
+  if ((e = launch_label_src<TH, LabelT, false, false, Src, kXY>(src, ntiles, st))) return e;
   if (ev && (e = cudaEventRecord(ev[1], st))) return e;
   if ((e = launch_merge_src<TH, LabelT>(src, ntiles, st))) return e;
   if ((e = launch_resolve_src<TH, LabelT>(src, ntiles, st))) return e;
   if (ev && (e = cudaEventRecord(ev[2], st))) return e;
-  if ((e = launch_recolor_src<TH, LabelT, false>(src, ntiles, (LabelT*)nullptr, st))) return e;
+  if ((e = launch_recolor_src<TH, LabelT, false, Src, kXY>(src, ntiles, (LabelT*)nullptr, st))) return e;
   if (ev) return cudaEventRecord(ev[3], st);
   return cudaSuccess;
 }
 
 // Dispatch on the tile height.
-template <typename LabelT, typename Src>
+template <typename LabelT, typename Src, bool kXY = false>
 cudaError_t sweep_th(uint32_t th, const Src& src, uint32_t ntiles, cudaStream_t st, cudaEvent_t* ev) {
   switch (th) {
-    case 16: return sweep_src<16, LabelT>(src, ntiles, st, ev);
-    case 32: return sweep_src<32, LabelT>(src, ntiles, st, ev);
-    case 64: return sweep_src<64, LabelT>(src, ntiles, st, ev);
+    case 16: return sweep_src<16, LabelT, Src, kXY>(src, ntiles, st, ev);
+    case 32: return sweep_src<32, LabelT, Src, kXY>(src, ntiles, st, ev);
+    case 64: return sweep_src<64, LabelT, Src, kXY>(src, ntiles, st, ev);
     default: return cudaErrorInvalidValue;
   }
 }

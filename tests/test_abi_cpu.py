@@ -66,3 +66,16 @@ def test_two_stage_labeller_rejects_bad_sub_lattices_before_device_work():
     for L, sub, bits in [(12, 5, 32), (12, 1, 32), (12, 24, 32), (1, 1, 32), (12, 6, 16),
                          (1 << 21, 1 << 20, 64), (1 << 17, 1 << 16, 32)]:
         assert f(L, sub, p, p, bits, None, None, None) == -1, (L, sub, bits)
+
+
+def test_xy_thresholds_match_the_oracle_table():
+    """The library's host-side XY bond table equals the oracle's, entry for
+    entry (same formula, same libm), for every M class and a range of T."""
+    for M in (2, 3, 4, 7, 64, 255, 256):
+        for T in (0.3, sw.T_KT, 1.7, 40.0):
+            assert np.array_equal(sw.xy_thresholds(M, T), oracle.xy_thresholds(M, T)), (M, T)
+    import ctypes
+    f = sw.lib().sw_xy_thresholds
+    out = (ctypes.c_uint32 * 4)()
+    for M, T in [(1, 1.0), (257, 1.0), (8, 0.0), (8, -1.0), (8, float("nan"))]:
+        assert f(M, T, out) == -1
