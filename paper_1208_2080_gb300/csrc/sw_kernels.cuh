@@ -90,6 +90,10 @@ struct LabelSmem {
   static constexpr int kObs = align16(kCnt + 4 * kNW);             // u32 [1 + 256]
   static constexpr int kCl = align16(kObs + 4 * 257);              // u16 [kTW*TH] root lists
   static constexpr int kBytes = align16(kCl + 2 * kTW * TH);
+  // XY form only: the bond thresholds of M <= 256 angles, lower triangle
+  // (129 * 130 / 2 entries), after the Potts layout
+  static constexpr int kXYTab = kBytes;
+  static constexpr int kXYBytes = align16(kXYTab + 4 * (129 * 130 / 2));
 };
 
 struct Lattice {
@@ -121,7 +125,7 @@ struct Bufs {
   uint32_t rk[20];            // Philox round keys of `seed` (see set_round_keys)
   // XY model (embedded clusters, M angles; q = 2 coins): 0 for Potts
   uint32_t M;
-  const uint32_t* tt;         // (M/2+1)^2 bond thresholds by |sigma| fold index
+  const uint32_t* tt;         // bond thresholds by |sigma| fold indices (c >= d): tt[c(c+1)/2 + d]
 };
 
 // The ten Philox round keys of a seed: (lo, hi) + r * (Weyl constants).
@@ -417,6 +421,13 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
   uint32_t bad = 0;
 
   for (int k = tid; k < 257; k += kThreads) sobs[k] = 0;
+  uint32_t* xtt = reinterpret_cast<uint32_t*>(smem + S::kXYTab);  // XY form only
+  if constexpr (kXY) {
+    static_assert(!Src::kMulti, "the XY form labels one lattice");
+    const Bufs& b0 = src.bufs(0);
+    const uint32_t H1 = (b0.M >> 1) + 1;
+    for (uint32_t k = tid; k < H1 * (H1 + 1) / 2; k += kThreads) xtt[k] = __ldg(b0.tt + k);
+  }
   uint32_t e_loc = 0, nsites = 0;
   uint32_t ncnt[3] = {0, 0, 0};
 
@@ -578,7 +589,11 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         uint32_t tr[4], td[4];
         if constexpr (kXY) {
           const uint16_t* xcls = reinterpret_cast<const uint16_t*>(sobs);
-          const uint32_t H1 = (b.M >> 1) + 1;
+          // threshold of fold indices (c, d): lower-triangle entry of the larger
+          auto thr_of = [&](uint32_t c, uint32_t d) -> uint32_t {
+            const uint32_t hi = c > d ? c : d, lo = c > d ? d : c;
+            return xtt[((hi * (hi + 1)) >> 1) + lo];
+          };
           uint32_t cs[5], cd[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
@@ -592,8 +607,8 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
             const uint32_t sg = cs[k] >> 8;
             eqr |= (sg != 0u && sg == (cs[k + 1] >> 8)) ? (1u << k) : 0u;
             eqd |= (sg != 0u && sg == (cd[k] >> 8)) ? (1u << k) : 0u;
-            tr[k] = __ldg(b.tt + (cs[k] & 0xFFu) * H1 + (cs[k + 1] & 0xFFu));
-            td[k] = __ldg(b.tt + (cs[k] & 0xFFu) * H1 + (cd[k] & 0xFFu));
+            tr[k] = thr_of(cs[k] & 0xFFu, cs[k + 1] & 0xFFu);
+            td[k] = thr_of(cs[k] & 0xFFu, cd[k] & 0xFFu);
           }
           eqr &= vm;
           eqd &= vm;

@@ -15,7 +15,7 @@ namespace swgb {
 template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY = false>
 cudaError_t configure_label(int* resident_out) {
   auto kern = k_label_tile<TH, LabelT, kGiven, kRoots, Src, kXY>;
-  const int smem = LabelSmem<TH>::kBytes;
+  const int smem = kXY ? LabelSmem<TH>::kXYBytes : LabelSmem<TH>::kBytes;
   static int resident = 0;
   if (!resident) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -38,7 +38,7 @@ cudaError_t configure_label(int* resident_out) {
 template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY = false>
 cudaError_t launch_label_src(const Src& src, uint32_t ntiles, cudaStream_t st) {
   auto kern = k_label_tile<TH, LabelT, kGiven, kRoots, Src, kXY>;
-  const int smem = LabelSmem<TH>::kBytes;
+  const int smem = kXY ? LabelSmem<TH>::kXYBytes : LabelSmem<TH>::kBytes;
   int resident = 0;
   cudaError_t e = configure_label<TH, LabelT, kGiven, kRoots, Src, kXY>(&resident);
   if (e != cudaSuccess) return e;

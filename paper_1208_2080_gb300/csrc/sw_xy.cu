@@ -53,50 +53,80 @@ void xy_table(uint32_t M, double T, uint32_t* tt) {
 
 // D[0..M/2] (bonds by folded angle difference) and n[0..M-1] (sites by
 // angle) of a configuration, accumulated into acc[0..M/2] and acc[M/2+1..].
-// Blocks over rows, one thread per group of 4 sites.
-__global__ void __launch_bounds__(256) k_xy_measure(const uint8_t* s, Lattice lat, uint32_t M,
-                                                    unsigned long long* acc) {
-  __shared__ uint32_t hist[kMaxAcc];
+// Blocks over rows; each warp counts into its own shared histogram (the
+// counts are shared-memory atomics, so warps do not contend with each
+// other); 16-site groups with 16-byte loads when L % 16 == 0, else 4-site
+// groups.
+constexpr int kMeasThreads = 256;
+__global__ void __launch_bounds__(kMeasThreads) k_xy_measure(const uint8_t* s, Lattice lat, uint32_t M,
+                                                             unsigned long long* acc) {
+  constexpr int kW = kMeasThreads / 32;
+  __shared__ uint32_t hist[kW][kMaxAcc];
   const uint32_t H = M >> 1, nacc = H + 1 + M;
-  for (uint32_t k = threadIdx.x; k < nacc; k += blockDim.x) hist[k] = 0;
+  for (uint32_t k = threadIdx.x; k < kW * kMaxAcc; k += blockDim.x) (&hist[0][0])[k] = 0;
   __syncthreads();
+  uint32_t* h = hist[threadIdx.x >> 5];
   const uint64_t L = lat.L;
-  const uint64_t groups = (L + 3) >> 2;
   auto fold = [&](uint32_t a, uint32_t b) -> uint32_t {
     const uint32_t t = a >= b ? a - b : a + M - b;
     return t < M - t ? t : M - t;
   };
-  for (uint64_t y = blockIdx.x; y < L; y += gridDim.x) {
-    const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
-    for (uint64_t gx = threadIdx.x; gx < groups; gx += blockDim.x) {
-      const uint64_t x = gx * 4;
-      uint32_t v = 0, vr = 0, vd = 0;
-      int nv = 4;
-      if (lat.vec4) {
-        v = *reinterpret_cast<const uint32_t*>(s + y * L + x);
-        const uint64_t xn = (x + 4 == L) ? 0 : x + 4;
-        vr = __funnelshift_r(v, *reinterpret_cast<const uint32_t*>(s + y * L + xn), 8);
-        vd = *reinterpret_cast<const uint32_t*>(s + yd * L + x);
-      } else {
-        nv = (int)((L - x) < 4 ? (L - x) : 4);
-        for (int k = 0; k < nv; ++k) {
-          const uint64_t xk = x + k, xr = (xk + 1 == L) ? 0 : xk + 1;
-          v |= (uint32_t)s[y * L + xk] << (8 * k);
-          vr |= (uint32_t)s[y * L + xr] << (8 * k);
-          vd |= (uint32_t)s[yd * L + xk] << (8 * k);
-        }
+  auto count4 = [&](uint32_t v, uint32_t vr, uint32_t vd, int nv) {
+    for (int k = 0; k < nv; ++k) {
+      const uint32_t a = (v >> (8 * k)) & 0xFFu;
+      atomicAdd(&h[H + 1 + a], 1u);
+      atomicAdd(&h[fold(a, (vr >> (8 * k)) & 0xFFu)], 1u);
+      atomicAdd(&h[fold(a, (vd >> (8 * k)) & 0xFFu)], 1u);
+    }
+  };
+  if ((L & 15u) == 0) {
+    const uint64_t g16 = L >> 4;
+    for (uint64_t y = blockIdx.x; y < L; y += gridDim.x) {
+      const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
+      for (uint64_t gx = threadIdx.x; gx < g16; gx += blockDim.x) {
+        const uint64_t x = gx * 16;
+        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(s + y * L + x));
+        const uint4 d = *reinterpret_cast<const uint4*>(s + yd * L + x);
+        const uint32_t nx = *reinterpret_cast<const uint32_t*>(s + y * L + ((x + 16 == L) ? 0 : x + 16));
+        const uint32_t w4[5] = {v.x, v.y, v.z, v.w, nx};
+        const uint32_t d4[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) count4(w4[k], __funnelshift_r(w4[k], w4[k + 1], 8), d4[k], 4);
       }
-      for (int k = 0; k < nv; ++k) {
-        const uint32_t a = (v >> (8 * k)) & 0xFFu;
-        atomicAdd(&hist[H + 1 + a], 1u);
-        atomicAdd(&hist[fold(a, (vr >> (8 * k)) & 0xFFu)], 1u);
-        atomicAdd(&hist[fold(a, (vd >> (8 * k)) & 0xFFu)], 1u);
+    }
+  } else {
+    const uint64_t groups = (L + 3) >> 2;
+    for (uint64_t y = blockIdx.x; y < L; y += gridDim.x) {
+      const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
+      for (uint64_t gx = threadIdx.x; gx < groups; gx += blockDim.x) {
+        const uint64_t x = gx * 4;
+        uint32_t v = 0, vr = 0, vd = 0;
+        int nv = 4;
+        if (lat.vec4) {
+          v = *reinterpret_cast<const uint32_t*>(s + y * L + x);
+          const uint64_t xn = (x + 4 == L) ? 0 : x + 4;
+          vr = __funnelshift_r(v, *reinterpret_cast<const uint32_t*>(s + y * L + xn), 8);
+          vd = *reinterpret_cast<const uint32_t*>(s + yd * L + x);
+        } else {
+          nv = (int)((L - x) < 4 ? (L - x) : 4);
+          for (int k = 0; k < nv; ++k) {
+            const uint64_t xk = x + k, xr = (xk + 1 == L) ? 0 : xk + 1;
+            v |= (uint32_t)s[y * L + xk] << (8 * k);
+            vr |= (uint32_t)s[y * L + xr] << (8 * k);
+            vd |= (uint32_t)s[yd * L + xk] << (8 * k);
+          }
+        }
+        count4(v, vr, vd, nv);
       }
     }
   }
   __syncthreads();
-  for (uint32_t k = threadIdx.x; k < nacc; k += blockDim.x)
-    if (hist[k]) atomicAdd(&acc[k], (unsigned long long)hist[k]);
+  for (uint32_t k = threadIdx.x; k < nacc; k += blockDim.x) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < kW; ++w) t += hist[w][k];
+    if (t) atomicAdd(&acc[k], (unsigned long long)t);
+  }
 }
 
 // Files the accumulated observables as configuration ctl[0] and clears them.
@@ -193,7 +223,7 @@ int xcheck(sw_xy* s) {
 cudaError_t xlaunch_measure(sw_xy* s) {
   uint64_t blocks = s->L;  // one block per row, at most 16 per SM
   if (blocks > 152ull * 16) blocks = 152ull * 16;
-  k_xy_measure<<<(unsigned)blocks, 256, 0, s->stream>>>(s->b.spin, s->lat, s->M, s->b.acc);
+  k_xy_measure<<<(unsigned)blocks, kMeasThreads, 0, s->stream>>>(s->b.spin, s->lat, s->M, s->b.acc);
   cudaError_t e = cudaGetLastError();
   if (e) return e;
   k_xy_commit<<<1, 128, 0, s->stream>>>(s->b, s->nacc);
@@ -258,6 +288,7 @@ int sw_xy_create(const sw_xy_params* prm, sw_xy** out) {
 
   const uint64_t nt = s->lat.ntiles;
   const size_t ntt = (size_t)(s->H + 1) * (s->H + 1);
+  const size_t ntri = (size_t)(s->H + 1) * (s->H + 2) / 2;  // lower triangle on the device
   const size_t rec = 1 + (size_t)s->nacc;
   Bufs& b = s->b;
   b.spin = (uint8_t*)xtake(s, s->N + 16);
@@ -273,7 +304,7 @@ int sw_xy_create(const sw_xy_params* prm, sw_xy** out) {
   b.ring = (unsigned long long*)xtake(s, (size_t)s->ring * rec * 8);
   b.ctl = (unsigned long long*)xtake(s, 64);
   b.err = (uint32_t*)xtake(s, 64);
-  uint32_t* tt = (uint32_t*)xtake(s, ntt * 4);
+  uint32_t* tt = (uint32_t*)xtake(s, ntri * 4);
   if (!b.spin || !b.code || !b.T || !b.edge || !b.ebits || !b.olist || !b.ocnt || !b.nso || !b.acc ||
       !b.ring || !b.ctl || !b.err || !tt) {
     xrelease(s);
@@ -289,9 +320,12 @@ int sw_xy_create(const sw_xy_params* prm, sw_xy** out) {
   b.M = s->M;
   b.tt = tt;
 
-  std::vector<uint32_t> host_tt(ntt);
+  std::vector<uint32_t> host_tt(ntt), host_tri(ntri);
   xy_table(s->M, prm->T, host_tt.data());
-  cudaError_t e = cudaMemcpyAsync(tt, host_tt.data(), ntt * 4, cudaMemcpyHostToDevice, s->stream);
+  for (uint32_t c = 0; c <= s->H; ++c)
+    for (uint32_t d = 0; d <= c; ++d) host_tri[c * (c + 1) / 2 + d] = host_tt[c * (s->H + 1) + d];
+  cudaError_t e = cudaMemcpyAsync(tt, host_tri.data(), ntri * 4, cudaMemcpyHostToDevice, s->stream);
+  if (!e) e = cudaStreamSynchronize(s->stream);  // host_tri is a stack-lifetime buffer
   if (!e) e = cudaMemsetAsync(b.T, 0, s->N * (lb / 8), s->stream);
   if (!e) e = cudaMemsetAsync(b.acc, 0, 8 * kMaxAcc, s->stream);
   if (!e) e = cudaMemsetAsync(b.ring, 0xFF, (size_t)s->ring * rec * 8, s->stream);
