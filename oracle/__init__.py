@@ -8,6 +8,8 @@ It wraps the plain C oracle in ``sw_oracle.c`` (conventions in
 Every function follows Sec. 2 of Komura & Okabe (Eq. 1 and the three SW
 steps); measurement follows Sec. 4 (Table 1, "update + measurement").
 
+The ``wolff_*`` functions wrap ``wolff_oracle.c``: the Wolff single-cluster
+update of the related work (Sec. 1), pinned in tests/test_oracle_wolff.py.
 The ``xy_*`` functions wrap ``xy_oracle.c``: the embedded-cluster sweep of
 the XY model with M angles that Sec. 5 names as the extension (Wolff's
 embedding), pinned in tests/test_oracle_xy.py.
@@ -73,6 +75,15 @@ def lib():
         L.orc_xy_run.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64,
                                  u8p, ctypes.c_uint32, ctypes.c_uint32, u64p, u64p]
         L.orc_xy_run.restype = ctypes.c_int
+        L.orc_wolff_seed.argtypes = [ctypes.c_uint64, ctypes.c_uint32, u8p, ctypes.c_uint64,
+                                     ctypes.c_uint32, u64p, u32p]
+        L.orc_wolff_seed.restype = None
+        L.orc_wolff_step.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                     ctypes.c_uint64, ctypes.c_uint32, u8p]
+        L.orc_wolff_step.restype = ctypes.c_uint64
+        L.orc_wolff_run.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
+                                    ctypes.c_uint64, u8p, ctypes.c_uint32, ctypes.c_uint32, u64p]
+        L.orc_wolff_run.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -261,3 +272,38 @@ def xy_magnetisation(n, M):
     n = np.asarray(n, dtype=np.float64)
     a = 2 * np.pi * np.arange(M) / M
     return (n * np.cos(a)).sum(-1), (n * np.sin(a)).sum(-1)
+
+
+# ---------------------------------------------------------------- Wolff
+# Single-cluster update of the q-state Potts model (related work, Sec. 1).
+# Conventions in wolff_oracle.h.
+
+def wolff_seed(spins, q, seed, t):
+    """(i0, s_new) of step t."""
+    s = np.ascontiguousarray(spins, dtype=np.uint8)
+    L = s.shape[0]
+    i0 = ctypes.c_uint64()
+    sn = ctypes.c_uint32()
+    lib().orc_wolff_seed(L, q, _p(s, ctypes.c_uint8), seed, t, ctypes.byref(i0), ctypes.byref(sn))
+    return int(i0.value), int(sn.value)
+
+
+def wolff_step(spins, q, T, seed, t):
+    """One step on a copy of spins; returns (new spins, cluster size)."""
+    s = np.array(spins, dtype=np.uint8, copy=True, order="C")
+    L = s.shape[0]
+    c = lib().orc_wolff_step(L, q, threshold(T), seed, t, _p(s, ctypes.c_uint8))
+    return s, int(c)
+
+
+def wolff_run(L, q, T, seed, nsteps, spins=None, t0=0):
+    """nsteps Wolff steps from spins (default: the init stream); returns
+    (spins, cluster sizes)."""
+    s = init_spins(L, q, seed).reshape(-1).copy() if spins is None else \
+        np.array(spins, dtype=np.uint8, copy=True).reshape(-1)
+    sizes = np.zeros(max(nsteps, 1), dtype=np.uint64)
+    rc = lib().orc_wolff_run(L, q, float(T), seed, _p(s, ctypes.c_uint8), t0, nsteps,
+                             _p(sizes, ctypes.c_uint64))
+    if rc != 0:
+        raise ValueError(f"orc_wolff_run failed ({rc})")
+    return s.reshape(L, L), sizes[:nsteps]

@@ -8,8 +8,8 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRCS = [os.path.join(HERE, f) for f in ("sw_oracle.c", "xy_oracle.c")]
-HDRS = [os.path.join(HERE, f) for f in ("sw_oracle.h", "xy_oracle.h")]
+SRCS = [os.path.join(HERE, f) for f in ("sw_oracle.c", "xy_oracle.c", "wolff_oracle.c")]
+HDRS = [os.path.join(HERE, f) for f in ("sw_oracle.h", "xy_oracle.h", "wolff_oracle.h")]
 LIB = os.path.join(HERE, "liboracle_sw.so")
 
 

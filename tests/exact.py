@@ -207,3 +207,38 @@ def xy_transition(L, M, T, label_fn):
                     s2 = np.where(flip == 1, refl[j][s], s)
                     P[si, int(s2 @ powers)] += w / (1 << nc)
     return P, H
+
+
+def wolff_transition(L, q, p):
+    """Exact transition matrix of one Wolff single-cluster step of the
+    q-state Potts model on the L x L torus: seed uniform over the N sites,
+    new state uniform over the q - 1 others, every bond between two sites in
+    the seed's state active with probability p independently; the seed's
+    component (breadth-first search) takes the new state."""
+    N = L * L
+    states, E, _ = e_sat_all(L, q)
+    S = len(states)
+    r_idx, d_idx = neighbours(L)
+    powers = q ** np.arange(N - 1, -1, -1)
+    P = np.zeros((S, S))
+    for si in range(S):
+        s = states[si]
+        for i0 in range(N):
+            old = s[i0]
+            el = [(i, d) for i in range(N) for d, nb in ((0, r_idx[i]), (1, d_idx[i]))
+                  if s[i] == old and s[nb] == old]
+            for mask in range(1 << len(el)):
+                k = bin(mask).count("1")
+                w = p ** k * (1 - p) ** (len(el) - k) / N
+                b = np.zeros(N, dtype=np.uint8)
+                for t, (i, d) in enumerate(el):
+                    if (mask >> t) & 1:
+                        b[i] |= RIGHT if d == 0 else DOWN
+                roots = bfs_roots(b.reshape(L, L)).ravel()
+                comp = roots == roots[i0]
+                for new in range(q):
+                    if new == old:
+                        continue
+                    s2 = np.where(comp, new, s)
+                    P[si, int(s2 @ powers)] += w / (q - 1)
+    return P, E
