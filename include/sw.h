@@ -370,6 +370,44 @@ int sw_xy_profile_read(sw_xy *xy, double *ms, uint64_t *launches, int nphase);
 int sw_xy_last_error(const sw_xy *xy);
 
 /* ---------------------------------------------------------------------------
+ * Wolff single-cluster update of the q-state Potts model (the comparison
+ * workload of the paper's related work, Sec. 1: one cluster per step, grown
+ * by processing the newly added spins in parallel).  One step t:
+ *   (1) seed i0 = floor(w0 N / 2^32), new state s_new = (s_old + 1 +
+ *       floor(w1 (q-1) / 2^32)) mod q, from words 0 and 1 of Philox counter
+ *       (0, 0, t, 4) (key = seed);
+ *   (2) the cluster: the connected component of i0 among the bonds between
+ *       sites in state s_old whose word u < thr (thr as sw_threshold; u the
+ *       word 2*(o&1)+dir of counter (o>>1, t, 5), o the site owning the bond,
+ *       dir 0 right / 1 down);
+ *   (3) every cluster site takes s_new.
+ * L is at most 32768 (site indices below 2^30).  Three kernels per step.
+ * ------------------------------------------------------------------------- */
+typedef struct sw_wolff sw_wolff;
+/* init: SW_INIT_RANDOM (the Potts init stream) or SW_INIT_ZERO; ring: steps
+ * whose cluster sizes are kept (0 = 1024).  Allocates N spins and an N-slot
+ * queue of uint32 site indices. */
+int sw_wolff_create(uint64_t L, uint32_t q, double T, uint64_t seed,
+                    uint32_t init, uint32_t ring, sw_wolff **out);
+void sw_wolff_destroy(sw_wolff *w);
+int sw_wolff_bind_stream(sw_wolff *w, void *stream);
+/* n steps (asynchronous). */
+int sw_wolff_step(sw_wolff *w, uint64_t n);
+/* Reads the device error word: SW_ERR_TIMEOUT if a growth wait hit its
+ * bound, SW_ERR_DEVICE on another device-side failure. */
+int sw_wolff_sync(sw_wolff *w);
+/* Cluster sizes of steps first .. first+count-1 (0-based) into a host
+ * array; SW_ERR_RANGE outside the ring window.  Synchronises. */
+int sw_wolff_sizes(sw_wolff *w, uint64_t first, uint64_t count,
+                   uint64_t *sizes);
+/* Copy the N spins out / in (host or device buffer); set_spins leaves the
+ * lattice unchanged and returns SW_ERR_INVAL if a spin is >= q. */
+int sw_wolff_spins(sw_wolff *w, uint8_t *dst, uint64_t n, int dst_on_device);
+int sw_wolff_set_spins(sw_wolff *w, const uint8_t *src, uint64_t n,
+                       int src_on_device);
+int sw_wolff_get_step(const sw_wolff *w, uint64_t *step);
+
+/* ---------------------------------------------------------------------------
  * Surrogate network (not in the paper): a 3 -> 64 -> 64 -> 64 -> 4 tanh MLP
  * with bfloat16 weights and fp32 accumulation that maps (q, log2 L, T/T_c)
  * to standardised observables and only places temperature grids.

@@ -3,10 +3,10 @@
 The computation lives in libswgb.so (CUDA, sm_103a; C ABI in include/sw.h);
 this package is its thin Python binding.  See ``Sim`` (one lattice),
 ``Batch`` (replicas), ``XY`` (embedded-cluster sweep of the XY model with M
-angles), ``label_bonds`` (labelling step alone) and ``threshold``.
+angles), ``Wolff`` (single-cluster updates), ``label_bonds`` (labelling step alone) and ``threshold``.
 """
 from ._binding import (  # noqa: F401
-    EXPORTS, LIB_PATH, XY, Batch, Mlp, Sim, SwError, check, label_bonds, label_bonds_2stage,
+    EXPORTS, LIB_PATH, XY, Batch, Wolff, Mlp, Sim, SwError, check, label_bonds, label_bonds_2stage,
     label_bonds_le, label_bonds_static, lib, pack_bonds, strerror, threshold, unpack_bonds,
     use_cuda_malloc, use_torch_allocator, xy_thresholds,
 )

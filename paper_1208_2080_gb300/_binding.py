@@ -41,6 +41,8 @@ EXPORTS = [
     "sw_xy_thresholds", "sw_xy_create", "sw_xy_destroy", "sw_xy_bind_stream", "sw_xy_sweep",
     "sw_xy_sync", "sw_xy_series", "sw_xy_spins", "sw_xy_set_spins", "sw_xy_get_sweep",
     "sw_xy_profile", "sw_xy_profile_read", "sw_xy_last_error",
+    "sw_wolff_create", "sw_wolff_destroy", "sw_wolff_bind_stream", "sw_wolff_step", "sw_wolff_sync",
+    "sw_wolff_sizes", "sw_wolff_spins", "sw_wolff_set_spins", "sw_wolff_get_step",
 ]
 
 
@@ -170,6 +172,15 @@ def lib():
         "sw_xy_profile": (i32, [vp, i32]),
         "sw_xy_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), u64p, i32]),
         "sw_xy_last_error": (i32, [vp]),
+        "sw_wolff_create": (i32, [u64, u32, ctypes.c_double, u64, u32, u32, ctypes.POINTER(vp)]),
+        "sw_wolff_destroy": (None, [vp]),
+        "sw_wolff_bind_stream": (i32, [vp, vp]),
+        "sw_wolff_step": (i32, [vp, u64]),
+        "sw_wolff_sync": (i32, [vp]),
+        "sw_wolff_sizes": (i32, [vp, u64, u64, u64p]),
+        "sw_wolff_spins": (i32, [vp, vp, u64, i32]),
+        "sw_wolff_set_spins": (i32, [vp, vp, u64, i32]),
+        "sw_wolff_get_step": (i32, [vp, u64p]),
         "sw_label_bonds_2stage": (i32, [u64, u64, vp, vp, u32, ctypes.POINTER(ctypes.c_uint32),
                                         ctypes.POINTER(ctypes.c_float), vp]),
     }
@@ -468,6 +479,73 @@ class XY:
     @property
     def handle(self):
         return self._h
+
+
+class Wolff:
+    """Wolff single-cluster updates of the q-state Potts model on an L x L
+    lattice (include/sw.h, sw_wolff_*)."""
+
+    def __init__(self, L, q, T, seed, *, init="random", ring=0, stream=None):
+        if not _allocator_chosen:
+            use_torch_allocator()
+        h = ctypes.c_void_p()
+        self._h = None
+        check(lib().sw_wolff_create(int(L), int(q), float(T), int(seed),
+                                    SW_INIT_ZERO if init == "zero" else SW_INIT_RANDOM, int(ring),
+                                    ctypes.byref(h)), "sw_wolff_create")
+        self._h = h
+        self.L, self.q, self.T, self.seed = int(L), int(q), float(T), int(seed)
+        self.N = self.L * self.L
+        if stream is not False:
+            self.bind_stream(stream)
+
+    def close(self):
+        if self._h is not None:
+            lib().sw_wolff_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def bind_stream(self, stream=None):
+        check(lib().sw_wolff_bind_stream(self._h, _stream_handle(stream)), "sw_wolff_bind_stream")
+
+    def step(self, n=1):
+        check(lib().sw_wolff_step(self._h, int(n)), "sw_wolff_step")
+
+    def sync(self):
+        check(lib().sw_wolff_sync(self._h), "sw_wolff_sync")
+
+    def sizes(self, first, count):
+        out = np.zeros(count, dtype=np.uint64)
+        check(lib().sw_wolff_sizes(self._h, int(first), int(count),
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))), "sw_wolff_sizes")
+        return out
+
+    def spins(self):
+        a = np.empty(self.N, dtype=np.uint8)
+        check(lib().sw_wolff_spins(self._h, a.ctypes.data_as(ctypes.c_void_p), self.N, 0), "sw_wolff_spins")
+        return a.reshape(self.L, self.L)
+
+    def set_spins(self, src):
+        a = np.ascontiguousarray(np.asarray(src, dtype=np.uint8).reshape(-1))
+        check(lib().sw_wolff_set_spins(self._h, a.ctypes.data_as(ctypes.c_void_p), self.N, 0),
+              "sw_wolff_set_spins")
+
+    @property
+    def step_count(self):
+        v = ctypes.c_uint64()
+        check(lib().sw_wolff_get_step(self._h, ctypes.byref(v)), "sw_wolff_get_step")
+        return int(v.value)
 
 
 class Batch:

@@ -9,7 +9,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libswgb.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["sw_api.cu", "sw_batch.cu", "sw_static.cu", "sw_mlp.cu", "sw_le.cu", "sw_xy.cu"]
+SOURCES = ["sw_api.cu", "sw_batch.cu", "sw_static.cu", "sw_mlp.cu", "sw_le.cu", "sw_xy.cu", "sw_wolff.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

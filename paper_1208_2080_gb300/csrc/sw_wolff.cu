@@ -1,0 +1,435 @@
+// sw_wolff.cu -- C ABI of the Wolff single-cluster update of the 2D q-state
+// Potts model (include/sw.h, sw_wolff_*), the comparison workload of the
+// paper's related work (Sec. 1: Wolff's single-cluster algorithm, grown on
+// a GPU by processing the newly added spins in parallel).
+//
+// One step: k_wolff_seed picks the seed site and the new state and puts
+// the seed in the queue; k_wolff_grow grows the cluster with every warp of a
+// persistent grid taking queued sites, testing their four neighbours
+// (state, then the bond's Philox word), claiming a joining neighbour with a
+// compare-and-swap of its spin (old state -> new state) and appending it;
+// k_wolff_finish files the cluster size.  Every bond has one fixed Philox
+// word per step, so the cluster is the connected component of the seed
+// among the active bonds whatever order the warps visit it in: the result
+// is bit-identical to the sequential oracle.
+//
+// The queue has one slot per site.  Warps reserve slots ahead of the
+// producers (atomic head), wait for them to be written, and reset each slot
+// they consume so the queue is empty again for the next step.  The growth
+// ends when every appended site has been processed (processed == tail,
+// both monotone); every wait is bounded and reports SW_ERR_TIMEOUT instead
+// of spinning on.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/sw.h"
+#include "philox.cuh"
+#include "sw_internal.h"
+
+using namespace swgb;
+
+namespace {
+
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // a free queue slot (site indices are < 2^30)
+constexpr uint32_t kDomSeed = 4, kDomWolffBond = 5;
+constexpr int kGrowThreads = 256;
+constexpr uint32_t kIdleCap = 1u << 22;   // idle polls of one warp before it gives up
+constexpr uint32_t kErrWolffTimeout = 1u, kErrWolffCas = 2u;
+
+struct WolffCtl {
+  uint32_t head, tail, processed, s_old;
+  uint32_t s_new, err, pad0, pad1;
+  unsigned long long step;
+};
+
+struct WolffArgs {
+  uint8_t* spin;
+  uint32_t* queue;
+  WolffCtl* ctl;
+  unsigned long long* sizes;  // ring of cluster sizes
+  uint32_t L, q, thr, ring;
+  uint64_t N;
+  uint32_t rk[20];
+};
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
+  return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+__global__ void k_wolff_seed(const __grid_constant__ WolffArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  WolffCtl* c = a.ctl;
+  const uint32_t t = (uint32_t)c->step;
+  const Words4 w = stream4_rk(a.rk, 0ull, t, kDomSeed);
+  const uint64_t i0 = ((uint64_t)w.x * a.N) >> 32;
+  const uint32_t old = a.spin[i0];
+  const uint32_t sn = (old + 1u + pick_state(w.y, a.q - 1u)) % a.q;
+  a.spin[i0] = (uint8_t)sn;
+  a.queue[0] = (uint32_t)i0;
+  c->head = 0;
+  c->tail = 1;
+  c->processed = 0;
+  c->s_old = old;
+  c->s_new = sn;
+}
+
+// Claims site j for the cluster: its spin byte goes from s_old to s_new in
+// one compare-and-swap of the aligned word that holds it.  False if j is not
+// (or no longer) in the old state.
+__device__ __forceinline__ bool claim(uint8_t* spin, uint64_t j, uint32_t s_old, uint32_t s_new,
+                                      uint32_t* err) {
+  uint32_t* wp = reinterpret_cast<uint32_t*>(spin + (j & ~3ull));
+  const uint32_t sh = 8u * (uint32_t)(j & 3u);
+  uint32_t w = ld_volatile(wp);
+  for (int it = 0; it < 64; ++it) {
+    if (((w >> sh) & 0xFFu) != s_old) return false;
+    const uint32_t nw = (w & ~(0xFFu << sh)) | (s_new << sh);
+    const uint32_t prev = atomicCAS(wp, w, nw);
+    if (prev == w) return true;
+    w = prev;  // a neighbouring byte changed (or this one was claimed): retry
+  }
+  atomicOr(err, kErrWolffCas);
+  return false;
+}
+
+__global__ void __launch_bounds__(kGrowThreads) k_wolff_grow(const __grid_constant__ WolffArgs a) {
+  constexpr unsigned kFull = 0xFFFFFFFFu;
+  WolffCtl* c = a.ctl;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t s_old = c->s_old, s_new = c->s_new;
+  const uint32_t t = (uint32_t)c->step;
+  const uint64_t L = a.L;
+  uint64_t slot = ~0ull;  // the queue slot this lane waits on
+  uint32_t idle = 0, nap = 32;
+  while (true) {
+    // lanes without a slot reserve the next ones
+    const unsigned need = __ballot_sync(kFull, slot == ~0ull);
+    if (need) {
+      uint32_t base = 0;
+      if (lane == (uint32_t)(__ffs(need) - 1)) base = atomicAdd(&c->head, (uint32_t)__popc(need));
+      base = __shfl_sync(kFull, base, __ffs(need) - 1);
+      if (slot == ~0ull) slot = base + __popc(need & ((1u << lane) - 1u));
+    }
+    // take the item of the slot if it has been written
+    uint32_t item = kEmpty;
+    if (slot < a.N) {
+      item = ld_volatile(a.queue + slot);
+      if (item != kEmpty) {
+        a.queue[slot] = kEmpty;  // consumed: the queue is empty again after the step
+        slot = ~0ull;
+      }
+    }
+    const bool have = item != kEmpty;
+    const unsigned got = __ballot_sync(kFull, have);
+    if (!got) {
+      // nothing to do: stop once every appended site has been processed
+      uint32_t done = 0;
+      if (lane == 0) {
+        const uint32_t p = ld_volatile(&c->processed);
+        __threadfence();
+        const uint32_t tl = ld_volatile(&c->tail);
+        done = (p == tl) ? 1u : 0u;
+      }
+      if (__shfl_sync(kFull, done, 0)) return;
+      if (++idle >= kIdleCap) {
+        if (lane == 0) atomicOr(&c->err, kErrWolffTimeout);
+        return;
+      }
+      __nanosleep(nap);
+      if (nap < 1024) nap *= 2;
+      continue;
+    }
+    idle = 0;
+    nap = 32;
+    // grow from the item: four neighbours, the bond that joins each
+    uint32_t add[4];
+    uint32_t nadd = 0;
+    if (have) {
+      const uint64_t i = item;
+      const uint64_t y = i / L, x = i - y * L;
+      const uint64_t xr = (x + 1 == L) ? 0 : x + 1, xl = x ? x - 1 : L - 1;
+      const uint64_t yd = (y + 1 == L) ? 0 : y + 1, yu = y ? y - 1 : L - 1;
+      const uint64_t nb[4] = {y * L + xr, y * L + xl, yd * L + x, yu * L + x};
+      const uint64_t own[4] = {i, y * L + xl, i, yu * L + x};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint64_t j = nb[k];
+        if (a.spin[j] != s_old) continue;  // already in the cluster, or another state
+        const Words4 w = stream4_rk(a.rk, own[k] >> 1, t, kDomWolffBond);
+        const uint32_t word = (own[k] & 1u) ? ((k >= 2) ? w.w : w.z) : ((k >= 2) ? w.y : w.x);
+        if (word >= a.thr) continue;
+        if (claim(a.spin, j, s_old, s_new, &c->err)) add[nadd++] = (uint32_t)j;
+      }
+    }
+    // append the claimed sites (one atomic per warp), then count the
+    // processed items: appends are visible in tail before processed moves
+    uint32_t off = nadd;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(kFull, off, o);
+      if (lane >= (uint32_t)o) off += v;
+    }
+    const uint32_t total = __shfl_sync(kFull, off, 31);
+    uint32_t pos = 0;
+    if (total) {
+      if (lane == 31) pos = atomicAdd(&c->tail, total);
+      pos = __shfl_sync(kFull, pos, 31);
+      const uint32_t mine = pos + off - nadd;
+      for (uint32_t k = 0; k < nadd; ++k) {
+        if (mine + k < a.N)
+          a.queue[mine + k] = add[k];
+        else
+          atomicOr(&c->err, kErrWolffCas);  // unreachable: every site joins at most once
+      }
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicAdd(&c->processed, (uint32_t)__popc(got));
+  }
+}
+
+__global__ void k_wolff_finish(const __grid_constant__ WolffArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  WolffCtl* c = a.ctl;
+  const unsigned long long t = c->step;
+  a.sizes[t % a.ring] = c->tail;
+  c->step = t + 1;
+}
+
+}  // namespace
+
+struct sw_wolff {
+  uint64_t L = 0, N = 0;
+  uint32_t q = 0, ring = 1024;
+  double T = 0;
+  cudaStream_t stream = nullptr;
+  DeviceAllocator alloc{};
+  std::vector<std::pair<void*, size_t>> blocks;
+  WolffArgs a{};
+  uint64_t step = 0;
+  uint64_t valid_from = 0;  // first step whose size is held
+  int grid = 0;
+  int last_err = SW_OK;
+};
+
+namespace {
+
+void* wtake(sw_wolff* w, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = w->alloc.allocate(bytes);
+  if (p) w->blocks.emplace_back(p, bytes);
+  return p;
+}
+
+void wrelease(sw_wolff* w) {
+  for (auto& kv : w->blocks) w->alloc.release(kv.first, kv.second);
+  w->blocks.clear();
+}
+
+int wcuda(sw_wolff* w) {
+  cudaGetLastError();
+  w->last_err = SW_ERR_CUDA;
+  return SW_ERR_CUDA;
+}
+
+int wcheck(sw_wolff* w) {
+  uint32_t err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, &w->a.ctl->err, 4, cudaMemcpyDeviceToHost, w->stream);
+  if (!e) e = cudaStreamSynchronize(w->stream);
+  if (e) return wcuda(w);
+  if (err & kErrWolffTimeout) return w->last_err = SW_ERR_TIMEOUT;
+  if (err) return w->last_err = SW_ERR_DEVICE;
+  return SW_OK;
+}
+
+// k_check_spins of the Potts path, restated for this translation unit: sets
+// *bad if a spin is >= q.
+__global__ void k_wolff_check(const uint8_t* s, uint64_t N, uint32_t q, uint32_t* bad) {
+  uint32_t any = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x)
+    any |= s[i] >= q;
+  if (__any_sync(0xFFFFFFFFu, any != 0) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+}
+
+__global__ void k_wolff_init(uint8_t* s, uint64_t N, uint32_t q, const __grid_constant__ WolffArgs a) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+    const Words4 w = stream4_rk(a.rk, i >> 2, 0u, kDomInit);
+    const uint32_t v[4] = {w.x, w.y, w.z, w.w};
+    s[i] = (uint8_t)pick_state(v[i & 3], q);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int sw_wolff_create(uint64_t L, uint32_t q, double T, uint64_t seed, uint32_t init, uint32_t ring,
+                    sw_wolff** out) {
+  if (!out) return SW_ERR_INVAL;
+  *out = nullptr;
+  if (L < 2 || L > 32768 || q < 2 || q > 255 || !(T > 0.0) || !isfinite(T) || init > SW_INIT_ZERO)
+    return SW_ERR_INVAL;
+  sw_wolff* w = new (std::nothrow) sw_wolff();
+  if (!w) return SW_ERR_NOMEM;
+  w->L = L;
+  w->N = L * L;
+  w->q = q;
+  w->T = T;
+  w->ring = ring ? ring : 1024u;
+  w->alloc = current_allocator();
+  WolffArgs& a = w->a;
+  a.spin = (uint8_t*)wtake(w, w->N + 16);
+  a.queue = (uint32_t*)wtake(w, w->N * 4);
+  a.ctl = (WolffCtl*)wtake(w, sizeof(WolffCtl));
+  a.sizes = (unsigned long long*)wtake(w, (size_t)w->ring * 8);
+  if (!a.spin || !a.queue || !a.ctl || !a.sizes) {
+    wrelease(w);
+    delete w;
+    return SW_ERR_NOMEM;
+  }
+  a.L = (uint32_t)L;
+  a.N = w->N;
+  a.q = q;
+  a.thr = bond_threshold(T);
+  a.ring = w->ring;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    a.rk[2 * r] = k0;
+    a.rk[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wolff_grow, kGrowThreads, 0);
+  if (sms <= 0) sms = 152;
+  if (per_sm <= 0) per_sm = 1;
+  if (per_sm > 4) per_sm = 4;
+  w->grid = sms * per_sm;
+  cudaError_t e = cudaMemsetAsync(a.queue, 0xFF, w->N * 4, w->stream);
+  if (!e) e = cudaMemsetAsync(a.ctl, 0, sizeof(WolffCtl), w->stream);
+  if (!e) e = cudaMemsetAsync(a.sizes, 0, (size_t)w->ring * 8, w->stream);
+  if (!e) {
+    if (init == SW_INIT_ZERO) {
+      e = cudaMemsetAsync(a.spin, 0, w->N, w->stream);
+    } else {
+      k_wolff_init<<<152 * 8, 256, 0, w->stream>>>(a.spin, w->N, q, a);
+      e = cudaGetLastError();
+    }
+  }
+  if (!e) e = cudaStreamSynchronize(w->stream);
+  if (e) {
+    cudaGetLastError();
+    wrelease(w);
+    delete w;
+    return SW_ERR_CUDA;
+  }
+  *out = w;
+  return SW_OK;
+}
+
+void sw_wolff_destroy(sw_wolff* w) {
+  if (!w) return;
+  cudaStreamSynchronize(w->stream);
+  wrelease(w);
+  delete w;
+}
+
+int sw_wolff_bind_stream(sw_wolff* w, void* stream) {
+  if (!w) return SW_ERR_INVAL;
+  w->stream = (cudaStream_t)stream;
+  return SW_OK;
+}
+
+int sw_wolff_step(sw_wolff* w, uint64_t n) {
+  if (!w) return SW_ERR_INVAL;
+  if (w->last_err) return w->last_err;
+  for (uint64_t k = 0; k < n; ++k) {
+    k_wolff_seed<<<1, 32, 0, w->stream>>>(w->a);
+    k_wolff_grow<<<w->grid, kGrowThreads, 0, w->stream>>>(w->a);
+    k_wolff_finish<<<1, 32, 0, w->stream>>>(w->a);
+    if (cudaGetLastError() != cudaSuccess) return wcuda(w);
+  }
+  w->step += n;
+  return SW_OK;
+}
+
+int sw_wolff_sync(sw_wolff* w) {
+  if (!w) return SW_ERR_INVAL;
+  if (w->last_err) return w->last_err;
+  return wcheck(w);
+}
+
+int sw_wolff_sizes(sw_wolff* w, uint64_t first, uint64_t count, uint64_t* sizes) {
+  if (!w || (count && !sizes)) return SW_ERR_INVAL;
+  if (w->last_err) return w->last_err;
+  if (count == 0) return SW_OK;
+  const uint64_t last = first + count - 1;
+  if (last < first || last >= w->step) return SW_ERR_RANGE;
+  uint64_t oldest = w->valid_from;
+  if (w->step > w->ring && w->step - w->ring > oldest) oldest = w->step - w->ring;
+  if (first < oldest) return SW_ERR_RANGE;
+  std::vector<unsigned long long> host(w->ring);
+  if (cudaMemcpyAsync(host.data(), w->a.sizes, (size_t)w->ring * 8, cudaMemcpyDeviceToHost, w->stream))
+    return wcuda(w);
+  int rc = wcheck(w);
+  if (rc) return rc;
+  for (uint64_t k = 0; k < count; ++k) sizes[k] = host[(first + k) % w->ring];
+  return SW_OK;
+}
+
+int sw_wolff_spins(sw_wolff* w, uint8_t* dst, uint64_t n, int dst_on_device) {
+  if (!w || !dst || n != w->N) return SW_ERR_INVAL;
+  if (w->last_err) return w->last_err;
+  if (cudaMemcpyAsync(dst, w->a.spin, w->N, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                      w->stream))
+    return wcuda(w);
+  if (!dst_on_device) return wcheck(w);
+  return SW_OK;
+}
+
+int sw_wolff_set_spins(sw_wolff* w, const uint8_t* src, uint64_t n, int src_on_device) {
+  if (!w || !src || n != w->N) return SW_ERR_INVAL;
+  if (w->last_err) return w->last_err;
+  std::vector<uint8_t> keep;
+  cudaError_t e = cudaSuccess;
+  // validate in a scratch copy first so a bad configuration leaves the
+  // lattice as it was
+  uint8_t* tmp = (uint8_t*)w->alloc.allocate(((w->N + 16 + 255) / 256) * 256);
+  uint32_t* bad = (uint32_t*)w->alloc.allocate(256);
+  if (!tmp || !bad) {
+    if (tmp) w->alloc.release(tmp, ((w->N + 16 + 255) / 256) * 256);
+    if (bad) w->alloc.release(bad, 256);
+    return SW_ERR_NOMEM;
+  }
+  e = cudaMemcpyAsync(tmp, src, w->N, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                      w->stream);
+  if (!e) e = cudaMemsetAsync(bad, 0, 4, w->stream);
+  if (!e) {
+    k_wolff_check<<<152 * 8, 256, 0, w->stream>>>(tmp, w->N, w->q, bad);
+    e = cudaGetLastError();
+  }
+  uint32_t hbad = 0;
+  if (!e) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, w->stream);
+  if (!e) e = cudaStreamSynchronize(w->stream);
+  if (!e && !hbad) e = cudaMemcpyAsync(w->a.spin, tmp, w->N, cudaMemcpyDeviceToDevice, w->stream);
+  if (!e) e = cudaStreamSynchronize(w->stream);
+  w->alloc.release(tmp, ((w->N + 16 + 255) / 256) * 256);
+  w->alloc.release(bad, 256);
+  if (e) return wcuda(w);
+  return hbad ? SW_ERR_INVAL : SW_OK;
+}
+
+int sw_wolff_get_step(const sw_wolff* w, uint64_t* step) {
+  if (!w || !step) return SW_ERR_INVAL;
+  *step = w->step;
+  return SW_OK;
+}
+
+}  // extern "C"

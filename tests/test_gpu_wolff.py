@@ -1,0 +1,60 @@
+"""GPU parity of the Wolff single-cluster update (sw_wolff_*): spins and
+cluster sizes bit-identical to the CPU oracle (wolff_oracle.c)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1208_2080_gb300 as sw
+
+pytestmark = pytest.mark.gpu
+
+
+def _compare(L, q, T, seed, steps, init="random", spins=None):
+    s0 = oracle.init_spins(L, q, seed) if init == "random" else np.zeros((L, L), np.uint8)
+    if spins is not None:
+        s0 = spins
+    ref_s, ref_c = oracle.wolff_run(L, q, T, seed, steps, spins=s0)
+    with sw.Wolff(L, q, T, seed, init=init) as w:
+        if spins is not None:
+            w.set_spins(spins)
+        assert np.array_equal(w.spins(), s0)
+        w.step(steps)
+        c = w.sizes(0, steps)
+        got = w.spins()
+        w.sync()
+    assert np.array_equal(c, ref_c), (L, q, T)
+    assert np.array_equal(got, ref_s), (L, q, T)
+
+
+@pytest.mark.parametrize("L", [2, 3, 5, 16, 64, 100, 257])
+@pytest.mark.parametrize("q", [2, 3, 8])
+def test_matches_oracle(L, q):
+    T = sw.tc(q)
+    _compare(L, q, T, 100 * L + q, 30)
+    _compare(L, q, 0.7 * T, 100 * L + q + 1, 10, init="zero")
+
+
+def test_large_clusters_at_low_temperature():
+    """An ordered start at T_c / 2: nearly every step grows a cluster of most
+    of the lattice."""
+    L, q = 1024, 2
+    _compare(L, q, 0.5 * sw.tc(q), 3, 6, init="zero")
+
+
+def test_critical_run_against_oracle():
+    L, q = 512, 3
+    s0 = oracle.run(L, q, sw.tc(q), 17, 30)[0]  # roughly equilibrated by SW sweeps
+    _compare(L, q, sw.tc(q), 17, 40, spins=s0)
+
+
+def test_set_spins_rejects_bad_states():
+    with sw.Wolff(32, 3, 1.0, 1) as w:
+        s = w.spins()
+        bad = s.copy()
+        bad[3, 4] = 3
+        with pytest.raises(sw.SwError) as e:
+            w.set_spins(bad)
+        assert e.value.code == -1
+        assert np.array_equal(w.spins(), s)
+        w.step(3)
+        w.sync()
