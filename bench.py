@@ -319,6 +319,14 @@ def run_ours(args, rank, world):
         torch.cuda.empty_cache()
         batched = run_batched(args, sw, torch)
 
+    wolff = None
+    if args.wolff_steps > 0:
+        if sim is not None:
+            sim.close()
+            sim = None
+        torch.cuda.empty_cache()
+        wolff = run_wolff(args, sw, torch)
+
     xy = None
     if args.xy_sweeps > 0:
         if sim is not None:
@@ -367,6 +375,7 @@ def run_ours(args, rank, world):
         "observables_last": {"config": cfg, "E_sat": E, "n": [int(x) for x in n]},
         "batched": batched,
         "xy": xy,
+        "wolff": wolff,
     }
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
@@ -415,6 +424,53 @@ def run_xy(args, sw, torch):
             "phases": phases, "dominant": XY_PHASES[dom], "peak": peak, "peak_kind": peak_kind,
             "energy_per_site_last": float(-(D[0] * np.cos(2 * np.pi * np.arange(M // 2 + 1) / M)).sum()
                                           / N)}
+
+
+def run_wolff(args, sw, torch):
+    """The Wolff single-cluster comparison workload (q = 2, T_c): spin flips
+    per ns over timed steps from a configuration equilibrated by SW sweeps,
+    next to the SW sweep on the same lattice."""
+    import numpy as np
+    L, q = args.wolff_L, 2
+    N = L * L
+    T = sw.tc(q)
+    stream = torch.cuda.current_stream()
+    with sw.Sim(L, q, T, 21, init="zero") as s_:
+        s_.sweep(200)
+        s_.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s_.sweep(20)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sw_rate = N * 20 / (e0.elapsed_time(e1) * 1e6)
+        spins = s_.spins()
+    modes = {}
+    for mode, steps in (("label", args.wolff_steps), ("grow", max(1, args.wolff_steps // 5))):
+        with sw.Wolff(L, q, T, 22, mode=mode) as w:
+            w.set_spins(spins)
+            w.step(args.wolff_warmup)
+            w.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            w.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            sizes = w.sizes(args.wolff_warmup, steps).astype(np.float64)
+            w.sync()
+        flips = float(sizes.sum())
+        modes[mode] = {"value": flips / (ms * 1e6), "unit": "spin flips/ns", "steps": steps,
+                       "ms_per_step": ms / steps, "mean_cluster": flips / steps,
+                       "mean_cluster_over_N": flips / steps / N,
+                       "gpu_launches": (7 if mode == "label" else 3) * steps}
+    best = max(modes, key=lambda m: modes[m]["value"])
+    return {"workload": f"Wolff single-cluster, q=2, T=T_c, L={L}, from 200 SW sweeps of an all-zero "
+                        f"start, {args.wolff_warmup} warm-up steps",
+            "metric": "Wolff spin flips/ns", "value": modes[best]["value"], "unit": "spin flips/ns",
+            "best_mode": best, "modes": modes,
+            "sw_same_lattice": {"value": sw_rate, "unit": UNIT,
+                                "note": "SW sweep updates every site each sweep"}}
 
 
 def run_batched(args, sw, torch):
@@ -483,6 +539,9 @@ def main():
     ap.add_argument("--batch-R", type=int, default=512, help="replicas in the batched measurement")
     ap.add_argument("--batch-sweeps", type=int, default=40, help="0 skips the batched measurement")
     ap.add_argument("--plain-sweeps", type=int, default=10)
+    ap.add_argument("--wolff-steps", type=int, default=100, help="0 skips the Wolff measurement")
+    ap.add_argument("--wolff-warmup", type=int, default=10)
+    ap.add_argument("--wolff-L", type=int, default=16384)
     ap.add_argument("--xy-sweeps", type=int, default=20, help="0 skips the XY-model measurement")
     ap.add_argument("--xy-warmup", type=int, default=5)
     ap.add_argument("--xy-L", type=int, default=65536)

@@ -406,6 +406,16 @@ int sw_wolff_spins(sw_wolff *w, uint8_t *dst, uint64_t n, int dst_on_device);
 int sw_wolff_set_spins(sw_wolff *w, const uint8_t *src, uint64_t n,
                        int src_on_device);
 int sw_wolff_get_step(const sw_wolff *w, uint64_t *step);
+/* How the cluster is found (same result either way).  SW_WOLFF_GROW
+ * (default): persistent warps grow it from a site queue, work proportional
+ * to the cluster.  SW_WOLFF_LABEL: the step's active bonds over the whole
+ * lattice are labelled by the SW sweep's tile union-find and the sites with
+ * the seed's root flipped (the connected-component route of the related
+ * work); allocates the labelling buffers (about 11 B per site) on first
+ * use. */
+#define SW_WOLFF_GROW 0
+#define SW_WOLFF_LABEL 1
+int sw_wolff_set_mode(sw_wolff *w, int mode);
 
 /* ---------------------------------------------------------------------------
  * Surrogate network (not in the paper): a 3 -> 64 -> 64 -> 64 -> 4 tanh MLP

@@ -42,7 +42,7 @@ EXPORTS = [
     "sw_xy_sync", "sw_xy_series", "sw_xy_spins", "sw_xy_set_spins", "sw_xy_get_sweep",
     "sw_xy_profile", "sw_xy_profile_read", "sw_xy_last_error",
     "sw_wolff_create", "sw_wolff_destroy", "sw_wolff_bind_stream", "sw_wolff_step", "sw_wolff_sync",
-    "sw_wolff_sizes", "sw_wolff_spins", "sw_wolff_set_spins", "sw_wolff_get_step",
+    "sw_wolff_sizes", "sw_wolff_spins", "sw_wolff_set_spins", "sw_wolff_get_step", "sw_wolff_set_mode",
 ]
 
 
@@ -181,6 +181,7 @@ def lib():
         "sw_wolff_spins": (i32, [vp, vp, u64, i32]),
         "sw_wolff_set_spins": (i32, [vp, vp, u64, i32]),
         "sw_wolff_get_step": (i32, [vp, u64p]),
+        "sw_wolff_set_mode": (i32, [vp, i32]),
         "sw_label_bonds_2stage": (i32, [u64, u64, vp, vp, u32, ctypes.POINTER(ctypes.c_uint32),
                                         ctypes.POINTER(ctypes.c_float), vp]),
     }
@@ -485,7 +486,9 @@ class Wolff:
     """Wolff single-cluster updates of the q-state Potts model on an L x L
     lattice (include/sw.h, sw_wolff_*)."""
 
-    def __init__(self, L, q, T, seed, *, init="random", ring=0, stream=None):
+    GROW, LABEL = 0, 1
+
+    def __init__(self, L, q, T, seed, *, init="random", ring=0, mode="grow", stream=None):
         if not _allocator_chosen:
             use_torch_allocator()
         h = ctypes.c_void_p()
@@ -498,6 +501,13 @@ class Wolff:
         self.N = self.L * self.L
         if stream is not False:
             self.bind_stream(stream)
+        self.set_mode(mode)
+
+    def set_mode(self, mode):
+        """"grow" (cluster grown from a site queue) or "label" (whole-lattice
+        labelling of the step's bonds); both give the same clusters."""
+        check(lib().sw_wolff_set_mode(self._h, self.LABEL if mode == "label" else self.GROW),
+              "sw_wolff_set_mode")
 
     def close(self):
         if self._h is not None:

@@ -13,6 +13,13 @@
 // among the active bonds whatever order the warps visit it in: the result
 // is bit-identical to the sequential oracle.
 //
+// A second mode finds the same cluster by labelling (the route of the
+// related work's connected-component Wolff): k_wolff_bonds writes every
+// active bond of the step (both ends in the seed's old state, word below the
+// threshold), the tile union-find of the SW sweep labels them, and
+// k_wolff_flip gives the new state to the sites whose root is the seed's.
+// Its cost is that of labelling the lattice, independent of the cluster.
+//
 // The queue has one slot per site.  Warps reserve slots ahead of the
 // producers (atomic head), wait for them to be written, and reset each slot
 // they consume so the queue is empty again for the next step.  The growth
@@ -30,6 +37,8 @@
 #include "../../include/sw.h"
 #include "philox.cuh"
 #include "sw_internal.h"
+#include "sw_kernels.cuh"
+#include "sw_launch.cuh"
 
 using namespace swgb;
 
@@ -49,11 +58,13 @@ struct WolffCtl {
 
 struct WolffArgs {
   uint8_t* spin;
-  uint32_t* queue;
+  uint32_t* queue;            // growth mode
+  uint8_t* bonds;             // labelling mode: packed bonds of the step
+  uint32_t* roots;            // labelling mode: root of every site
   WolffCtl* ctl;
   unsigned long long* sizes;  // ring of cluster sizes
   uint32_t L, q, thr, ring;
-  uint64_t N;
+  uint64_t N, bp;
   uint32_t rk[20];
 };
 
@@ -61,7 +72,9 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
   return *reinterpret_cast<const volatile uint32_t*>(p);
 }
 
-__global__ void k_wolff_seed(const __grid_constant__ WolffArgs a) {
+// grow: also flips the seed and queues it (growth mode); otherwise the
+// seed index is kept in pad0 for the flip of the labelling mode.
+__global__ void k_wolff_seed(const __grid_constant__ WolffArgs a, int grow) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   WolffCtl* c = a.ctl;
   const uint32_t t = (uint32_t)c->step;
@@ -69,13 +82,60 @@ __global__ void k_wolff_seed(const __grid_constant__ WolffArgs a) {
   const uint64_t i0 = ((uint64_t)w.x * a.N) >> 32;
   const uint32_t old = a.spin[i0];
   const uint32_t sn = (old + 1u + pick_state(w.y, a.q - 1u)) % a.q;
-  a.spin[i0] = (uint8_t)sn;
-  a.queue[0] = (uint32_t)i0;
+  if (grow) {
+    a.spin[i0] = (uint8_t)sn;
+    a.queue[0] = (uint32_t)i0;
+  }
   c->head = 0;
-  c->tail = 1;
+  c->tail = grow ? 1 : 0;
   c->processed = 0;
   c->s_old = old;
   c->s_new = sn;
+  c->pad0 = (uint32_t)i0;
+}
+
+// Labelling mode, bonds of the step: a bond is active iff both ends are in
+// the seed's old state and its word is below the threshold.  A thread
+// writes the packed byte of 4 sites (bits 2k right, 2k+1 down).
+__global__ void __launch_bounds__(256) k_wolff_bonds(const __grid_constant__ WolffArgs a) {
+  const uint32_t s_old = a.ctl->s_old;
+  const uint32_t t = (uint32_t)a.ctl->step;
+  const uint64_t L = a.L, groups = a.bp;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L * groups;
+       g += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t y = g / groups, x0 = (g - y * groups) * 4;
+    const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
+    uint32_t byte = 0;
+    for (int k = 0; k < 4 && x0 + k < L; ++k) {
+      const uint64_t x = x0 + k, i = y * L + x;
+      if (a.spin[i] != s_old) continue;
+      const uint64_t xr = (x + 1 == L) ? 0 : x + 1;
+      const bool er = a.spin[y * L + xr] == s_old, ed = a.spin[yd * L + x] == s_old;
+      if (!er && !ed) continue;
+      const Words4 w = stream4_rk(a.rk, i >> 1, t, kDomWolffBond);
+      const uint32_t wr = (i & 1u) ? w.z : w.x, wd = (i & 1u) ? w.w : w.y;
+      if (er && wr < a.thr) byte |= 1u << (2 * k);
+      if (ed && wd < a.thr) byte |= 2u << (2 * k);
+    }
+    a.bonds[y * a.bp + x0 / 4] = (uint8_t)byte;
+  }
+}
+
+// Labelling mode, the update: sites whose root is the seed's take the new
+// state; the cluster size goes to ctl->tail.
+__global__ void __launch_bounds__(256) k_wolff_flip(const __grid_constant__ WolffArgs a) {
+  const uint32_t r0 = a.roots[a.ctl->pad0];
+  const uint32_t s_new = a.ctl->s_new;
+  uint32_t n = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    if (a.roots[i] == r0) {
+      a.spin[i] = (uint8_t)s_new;
+      ++n;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xFFFFFFFFu, n, o);
+  if ((threadIdx.x & 31) == 0 && n) atomicAdd(&a.ctl->tail, n);
 }
 
 // Claims site j for the cluster: its spin byte goes from s_old to s_new in
@@ -203,8 +263,16 @@ __global__ void k_wolff_finish(const __grid_constant__ WolffArgs a) {
 
 }  // namespace
 
+// Labelling-mode instantiations of the tile kernels, private to this file
+// (their launch set-up is not shared with the other translation units).
+struct WolffSrc : SingleSrc {};
+
 struct sw_wolff {
   uint64_t L = 0, N = 0;
+  int mode = SW_WOLFF_GROW;
+  uint32_t th = 64;
+  Lattice lat{};
+  Bufs lb{};  // labelling buffers (labelling mode)
   uint32_t q = 0, ring = 1024;
   double T = 0;
   cudaStream_t stream = nullptr;
@@ -238,12 +306,13 @@ int wcuda(sw_wolff* w) {
 }
 
 int wcheck(sw_wolff* w) {
-  uint32_t err = 0;
+  uint32_t err = 0, lerr = 0;
   cudaError_t e = cudaMemcpyAsync(&err, &w->a.ctl->err, 4, cudaMemcpyDeviceToHost, w->stream);
+  if (!e && w->a.roots) e = cudaMemcpyAsync(&lerr, w->lb.err, 4, cudaMemcpyDeviceToHost, w->stream);
   if (!e) e = cudaStreamSynchronize(w->stream);
   if (e) return wcuda(w);
-  if (err & kErrWolffTimeout) return w->last_err = SW_ERR_TIMEOUT;
-  if (err) return w->last_err = SW_ERR_DEVICE;
+  if ((err & kErrWolffTimeout) || (lerr & (kErrFind | kErrUnion))) return w->last_err = SW_ERR_TIMEOUT;
+  if (err || lerr) return w->last_err = SW_ERR_DEVICE;
   return SW_OK;
 }
 
@@ -281,6 +350,7 @@ int sw_wolff_create(uint64_t L, uint32_t q, double T, uint64_t seed, uint32_t in
   w->q = q;
   w->T = T;
   w->ring = ring ? ring : 1024u;
+  w->th = pick_tile_h(L, 0);
   w->alloc = current_allocator();
   WolffArgs& a = w->a;
   a.spin = (uint8_t*)wtake(w, w->N + 16);
@@ -347,11 +417,111 @@ int sw_wolff_bind_stream(sw_wolff* w, void* stream) {
   return SW_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+template <int TH>
+cudaError_t wolff_label(sw_wolff* w) {
+  WolffSrc src;
+  src.b = w->lb;
+  src.lat = w->lat;
+  cudaError_t e = launch_label_src<TH, uint32_t, true, true>(src, w->lat.ntiles, w->stream);
+  if (e) return e;
+  e = launch_merge_src<TH, uint32_t>(src, w->lat.ntiles, w->stream);
+  if (e) return e;
+  return launch_recolor_src<TH, uint32_t, true>(src, w->lat.ntiles, w->a.roots, w->stream);
+}
+
+// Allocates the labelling buffers on first use of the labelling mode.
+int wolff_label_setup(sw_wolff* w) {
+  if (w->a.roots) return SW_OK;
+  const uint32_t th = w->th;
+  w->lat = make_lattice(w->L, th);
+  const uint64_t nt = w->lat.ntiles;
+  Bufs& b = w->lb;
+  w->a.bp = w->lat.bp;
+  w->a.bonds = (uint8_t*)wtake(w, w->L * w->lat.bp + 16);
+  w->a.roots = (uint32_t*)wtake(w, w->N * 4);
+  b.bonds = w->a.bonds;
+  b.code = (uint16_t*)wtake(w, w->N * 2 + 16);
+  b.T = wtake(w, w->N * 4);
+  b.edge = (uint16_t*)wtake(w, nt * edge_u16(th) * 2);
+  b.ebits = (uint32_t*)wtake(w, nt * bit_words(th) * 4);
+  b.olist = (uint16_t*)wtake(w, nt * open_cap(th) * 2);
+  b.ocnt = (uint32_t*)wtake(w, nt * 4);
+  b.ctl = (unsigned long long*)wtake(w, 64);
+  b.err = (uint32_t*)wtake(w, 64);
+  b.q = 2;
+  b.measure = 0;
+  if (!w->a.bonds || !w->a.roots || !b.code || !b.T || !b.edge || !b.ebits || !b.olist || !b.ocnt ||
+      !b.ctl || !b.err) {
+    w->a.roots = nullptr;  // the blocks taken so far are freed with the handle
+    return SW_ERR_NOMEM;
+  }
+  cudaError_t e = cudaMemsetAsync(b.T, 0, w->N * 4, w->stream);
+  if (!e) e = cudaMemsetAsync(b.ctl, 0, 64, w->stream);
+  if (!e) e = cudaMemsetAsync(b.err, 0, 64, w->stream);
+  if (!e) e = cudaMemsetAsync(b.ocnt, 0, nt * 4, w->stream);
+  if (!e) {
+    switch (th) {
+      case 16: e = configure_label<16, uint32_t, true, true, WolffSrc>(nullptr); break;
+      case 32: e = configure_label<32, uint32_t, true, true, WolffSrc>(nullptr); break;
+      default: e = configure_label<64, uint32_t, true, true, WolffSrc>(nullptr); break;
+    }
+  }
+  if (!e) e = cudaStreamSynchronize(w->stream);
+  if (e) {
+    w->a.roots = nullptr;
+    return wcuda(w);
+  }
+  return SW_OK;
+}
+
+cudaError_t wolff_step_label(sw_wolff* w) {
+  k_wolff_seed<<<1, 32, 0, w->stream>>>(w->a, 0);
+  uint64_t items = w->L * w->a.bp, blocks = (items + 255) / 256;
+  if (blocks > 152ull * 16) blocks = 152ull * 16;
+  k_wolff_bonds<<<(unsigned)blocks, 256, 0, w->stream>>>(w->a);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
+  switch (w->th) {
+    case 16: e = wolff_label<16>(w); break;
+    case 32: e = wolff_label<32>(w); break;
+    default: e = wolff_label<64>(w); break;
+  }
+  if (e) return e;
+  blocks = (w->N + 255) / 256;
+  if (blocks > 152ull * 16) blocks = 152ull * 16;
+  k_wolff_flip<<<(unsigned)blocks, 256, 0, w->stream>>>(w->a);
+  k_wolff_finish<<<1, 32, 0, w->stream>>>(w->a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int sw_wolff_set_mode(sw_wolff* w, int mode) {
+  if (!w || (mode != SW_WOLFF_GROW && mode != SW_WOLFF_LABEL)) return SW_ERR_INVAL;
+  if (w->last_err) return w->last_err;
+  if (mode == SW_WOLFF_LABEL) {
+    int rc = wolff_label_setup(w);
+    if (rc) return rc;
+  }
+  w->mode = mode;
+  return SW_OK;
+}
+
 int sw_wolff_step(sw_wolff* w, uint64_t n) {
   if (!w) return SW_ERR_INVAL;
   if (w->last_err) return w->last_err;
   for (uint64_t k = 0; k < n; ++k) {
-    k_wolff_seed<<<1, 32, 0, w->stream>>>(w->a);
+    if (w->mode == SW_WOLFF_LABEL) {
+      if (wolff_step_label(w) != cudaSuccess) return wcuda(w);
+      continue;
+    }
+    k_wolff_seed<<<1, 32, 0, w->stream>>>(w->a, 1);
     k_wolff_grow<<<w->grid, kGrowThreads, 0, w->stream>>>(w->a);
     k_wolff_finish<<<1, 32, 0, w->stream>>>(w->a);
     if (cudaGetLastError() != cudaSuccess) return wcuda(w);
