@@ -140,3 +140,32 @@ def test_recolor_constant_on_clusters_and_drawn_at_root():
         w = oracle.philox([int(r) & 0xFFFFFFFF, int(r) >> 32, sweep, 1],
                           [seed & 0xFFFFFFFF, seed >> 32])[0]
         assert flat[r] == oracle.pick(w, q)
+
+
+def test_special_case_no_bonds_every_site_draws_its_own_state():
+    """thr = 0 (T -> infinity): no bond is active, every site is its own
+    root, and its new state is the pick of its own state word."""
+    L, q, seed, sweep = 7, 5, 12, 3
+    s = oracle.init_spins(L, q, seed)
+    T = 1e300
+    assert oracle.threshold(T) == 0
+    b = oracle.bonds(s, T, seed, sweep)
+    assert not b.any()
+    root = oracle.label(b)
+    assert np.array_equal(root.ravel(), np.arange(L * L))
+    s2 = oracle.recolor(s, root, q, seed, sweep)
+    want = [oracle.pick(int(oracle.philox([i, 0, sweep, 1], [seed, 0])[0]), q) for i in range(L * L)]
+    assert np.array_equal(s2.ravel(), np.array(want, dtype=np.uint8))
+
+
+def test_special_case_uniform_start_at_zero_temperature_is_one_cluster():
+    """thr = 2^32 - 1 and a uniform start: (almost surely) every bond is
+    active, one cluster rooted at site 0, and all spins take the pick of
+    site 0's state word."""
+    L, q, seed = 9, 3, 4
+    T = 1e-3
+    assert oracle.threshold(T) == 2 ** 32 - 1
+    s = np.full((L, L), 2, dtype=np.uint8)
+    s1, _, _ = oracle.run(L, q, T, seed, 1, spins=s)
+    want = oracle.pick(int(oracle.philox([0, 0, 0, 1], [seed, 0])[0]), q)
+    assert np.all(s1 == want)

@@ -84,3 +84,25 @@ def test_critical_energy_baxter(q, tol):
     u = -E / (L * L)
     m, s = _batch_mean(u, nb=20)
     assert abs(m + (1 + 1 / np.sqrt(q))) < 5 * s + tol
+
+
+def test_3x3_ising_state_histogram_chi_square():
+    """Every one of the 512 configurations of the 3 x 3 Ising torus is
+    visited with its Boltzmann probability (chi-square over the states, with
+    the sample thinned to near-independence)."""
+    L, q, T = 3, 2, oracle.tc(2)
+    states, E, _ = exact.e_sat_all(L, q)
+    w = np.exp((E - E.max()) / T)
+    w /= w.sum()
+    n = 100_000
+    s, _, _ = oracle.run(L, q, T, 77, 100, series=False)  # burn-in: sweeps 0..99
+    counts = np.zeros(len(states))
+    powers = 2 ** np.arange(L * L - 1, -1, -1)
+    for k in range(n):  # the configuration after every 3rd sweep
+        s, _, _ = oracle.run(L, q, T, 77, 3, spins=s, sweep0=100 + 3 * k, series=False)
+        counts[int(s.ravel().astype(np.int64) @ powers)] += 1
+    m = len(counts)
+    expect = counts.sum() * w
+    chi2 = ((counts - expect) ** 2 / expect).sum()
+    dof = m - 1
+    assert chi2 < dof + 6 * np.sqrt(2 * dof), (chi2, dof)
