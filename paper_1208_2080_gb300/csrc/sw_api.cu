@@ -505,18 +505,32 @@ int sw_spins(sw_sim* s, uint8_t* dst, uint64_t n, int dst_on_device) {
 int sw_set_spins(sw_sim* s, const uint8_t* src, uint64_t n, int src_on_device) {
   if (!s || !src || n != s->N) return SW_ERR_INVAL;
   if (sticky(s)) return s->last_err;
-  cudaError_t e = cudaMemcpyAsync(s->b.spin, src, s->N,
-                                  src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                  s->stream);
   // validate on the device: flag word ctl[3]
   uint32_t* bad = reinterpret_cast<uint32_t*>(s->b.ctl + 3);
-  if (!e) e = cudaMemsetAsync(bad, 0, 4, s->stream);
-  if (!e) {
-    uint64_t blocks = (s->N / 4 + 255) / 256;
-    if (blocks > 152ull * 8) blocks = 152ull * 8;
-    if (blocks == 0) blocks = 1;
-    k_check_spins<<<(unsigned)blocks, 256, 0, s->stream>>>(s->b.spin, s->N, s->q, bad);
+  cudaError_t e = cudaMemsetAsync(bad, 0, 4, s->stream);
+  // page-locked host memory with a device mapping: one kernel reads it,
+  // writes the lattice and validates (no separate copy and check passes)
+  const void* mapped = nullptr;
+  if (!src_on_device && ((uintptr_t)src & 15u) == 0) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, src) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer != nullptr)
+      mapped = at.devicePointer;
+    cudaGetLastError();
+  }
+  if (!e && mapped) {
+    k_copy_check_spins<<<152 * 8, 256, 0, s->stream>>>((const uint8_t*)mapped, s->b.spin, s->N, s->q, bad);
     e = cudaGetLastError();
+  } else if (!e) {
+    e = cudaMemcpyAsync(s->b.spin, src, s->N,
+                        src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream);
+    if (!e) {
+      uint64_t blocks = (s->N / 4 + 255) / 256;
+      if (blocks > 152ull * 8) blocks = 152ull * 8;
+      if (blocks == 0) blocks = 1;
+      k_check_spins<<<(unsigned)blocks, 256, 0, s->stream>>>(s->b.spin, s->N, s->q, bad);
+      e = cudaGetLastError();
+    }
   }
   uint32_t hbad = 0;
   if (!e) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s->stream);

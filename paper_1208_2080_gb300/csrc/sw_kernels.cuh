@@ -1260,6 +1260,45 @@ static __global__ void k_check_spins(const uint8_t* s, uint64_t N, uint32_t q, u
   if (__any_sync(0xFFFFFFFFu, any != 0) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
 }
 
+// Copies N spins from page-locked host memory (read through its device
+// mapping, 16 B per load, many loads in flight) into the lattice and checks
+// them on the way: *bad is set if a spin is >= q.  src and dst 16-byte
+// aligned.
+static __global__ void __launch_bounds__(256) k_copy_check_spins(const uint8_t* __restrict__ src,
+                                                                 uint8_t* __restrict__ dst, uint64_t N,
+                                                                 uint32_t q, uint32_t* bad) {
+  const uint32_t lim = q * 0x01010101u;
+  const uint64_t n16 = N >> 4;
+  const uint4* s16 = reinterpret_cast<const uint4*>(src);
+  uint4* d16 = reinterpret_cast<uint4*>(dst);
+  uint32_t any = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n16; i += 4 * stride) {  // four 16-byte loads in flight per thread
+    uint4 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = s16[i + k * stride];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      any |= __vcmpgeu4(v[k].x, lim) | __vcmpgeu4(v[k].y, lim) | __vcmpgeu4(v[k].z, lim) |
+             __vcmpgeu4(v[k].w, lim);
+      d16[i + k * stride] = v[k];
+    }
+  }
+  for (; i < n16; i += stride) {
+    const uint4 v = s16[i];
+    any |= __vcmpgeu4(v.x, lim) | __vcmpgeu4(v.y, lim) | __vcmpgeu4(v.z, lim) | __vcmpgeu4(v.w, lim);
+    d16[i] = v;
+  }
+  if (blockIdx.x == 0)
+    for (uint64_t j = (n16 << 4) + threadIdx.x; j < N; j += blockDim.x) {
+      const uint8_t v = src[j];
+      dst[j] = v;
+      any |= (v >= q);
+    }
+  if (__any_sync(0xFFFFFFFFu, any != 0) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+}
+
 // Files the accumulated observables as configuration ctl[0].
 static __global__ void k_commit(Bufs b) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {

@@ -278,3 +278,28 @@ def test_config_l8192_q234_1200_sweeps_match_oracle():
         u = -(E[200:].astype(np.float64) / (L * L)).mean()
         assert abs(u - g["u_mean"]) < 1e-12
         assert abs(u + (1 + 1 / np.sqrt(q))) < {2: 2e-3, 3: 5e-3, 4: 1.5e-2}[q]
+
+
+@pytest.mark.parametrize("L", [7, 64, 130])
+def test_set_spins_from_page_locked_host_memory(L):
+    """A page-locked host buffer goes through the mapped copy-and-check
+    kernel: same chain as from device memory, and a bad state is still
+    rejected without touching the sweep counter."""
+    import torch
+    q = 3
+    s0 = oracle.init_spins(L, q, 31)
+    pinned = torch.from_numpy(s0.reshape(-1).copy()).pin_memory()
+    ref, _, _ = oracle.run(L, q, sw.tc(q), 31, 4, spins=s0)
+    with sw.Sim(L, q, sw.tc(q), 31, init="zero") as s:
+        s.set_spins(pinned.numpy())
+        assert np.array_equal(s.spins(), s0)
+        s.sweep(4)
+        assert np.array_equal(s.spins(), ref)
+        pinned[L * L - 1] = q  # last byte: the tail loop when L*L % 16 != 0
+        with pytest.raises(sw.SwError) as e:
+            s.set_spins(pinned.numpy())
+        assert e.value.code == -1
+        pinned[L * L - 1] = 0
+        pinned[0] = 7
+        with pytest.raises(sw.SwError):
+            s.set_spins(pinned.numpy())
