@@ -1,32 +1,38 @@
 // sw_kernels.cuh -- sm_103a kernels of one Swendsen-Wang sweep.
 //
-// A sweep is three launches over a tiling of the L x L lattice into
+// A sweep is four launches over a tiling of the L x L lattice into
 // 128 x TH tiles (tile t = ty*ntx + tx, origin (128*tx, TH*ty); the last
 // tile row/column is ragged when TH or 128 does not divide L):
 //
-//   k_label_tile  (one CTA per tile)  Sec. 2 steps (1)+(2), tile-local part:
-//       stage the tile's uint8 spins plus a one-site right/down halo in
-//       shared memory; draw the bonds (Philox, one call per two sites);
-//       measure E_sat / n[s] of the configuration it reads (Sec. 4); label
-//       the tile with a shared-memory union-find: horizontal runs inside a
-//       warp's 128-site row come from one __ballot_sync, vertical bonds are
-//       atomicMin unions (redundant ones between the same two runs skipped);
-//       a cluster that touches the tile edge is "open", the others are
-//       complete and get their new state here (Sec. 2 step (3)), drawn once
-//       per cluster from their root = smallest site index.  Per site it
-//       writes a 16-bit code: 0x8000|state for a closed cluster, the local
-//       root index for an open one.  For the boundary pass it writes the
-//       local roots of the four edge lines, the cross-edge bond bits, the
-//       list of open local roots, and initialises their global labels.
+//   k_label_tile  (persistent; a CTA per tile at a time)  Sec. 2 steps
+//       (1)+(2), tile-local part: stage the tile's uint8 spins plus a
+//       one-site right/down halo in shared memory; draw the bonds (Philox,
+//       one call per two sites); measure E_sat / n[s] of the configuration
+//       it reads (Sec. 4); label the tile with a shared-memory union-find:
+//       horizontal runs inside a warp's 128-site row come from one
+//       __ballot_sync, vertical bonds are atomicMin unions (redundant ones
+//       between the same two runs skipped); a cluster that touches the tile
+//       edge is "open", the others are complete and get their new state
+//       here (Sec. 2 step (3)), drawn once per cluster from their root =
+//       smallest site index.  Per site it writes a 16-bit code: 0x8000|state
+//       for a closed cluster, the slot of its open root otherwise.  For the
+//       boundary pass it writes the local roots of the four edge lines, the
+//       cross-edge bond bits, the list of open local roots, and initialises
+//       their global labels.
 //   k_merge       Sec. 2 step (2), global part: the single-GPU analogue of
 //       the paper's boundary-only inter-GPU labelling (Sec. 3): for every
 //       active bond that crosses a tile edge (periodic wrap included) a
 //       lock-free atomicMin union of the two open roots' global labels
 //       (site indices, uint32 or uint64), lanes that would repeat the same
 //       union are merged with __match_any_sync.
-//   k_recolor     Sec. 2 step (3) for open clusters: each open local root
-//       finds (and compresses to) its global root, draws the cluster state;
-//       every site then writes its new uint8 spin.
+//   k_resolve     Sec. 2 step (3) for open clusters: each open local root
+//       finds (and compresses to) its global root and draws the cluster
+//       state.
+//   k_recolor     every site writes its new uint8 spin from its code.
+//
+// The XY form (kXY; Sec. 5, Wolff's embedded clusters) is the same sweep
+// with the embedded bond rule in k_label_tile and reflections in
+// k_recolor; clusters draw a coin (the state draw with q = 2).
 //
 // Union always links the larger root under the smaller one, so the final
 // root of every cluster is its smallest site index -- the Hoshen-Kopelman
