@@ -239,8 +239,12 @@ def run_ours(args, rank, world):
     sim = sw.Sim(L, q, T, seed, init="zero", label_bits=args.label_bits, tile_h=args.tile_h)
     info = sim.info()
     stream = torch.cuda.current_stream()
+    evw0, evw1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evw0.record(stream)
     sim.sweep(args.warmup)
+    evw1.record(stream)
     torch.cuda.synchronize()
+    warm_ms = evw0.elapsed_time(evw1)
 
     def barrier():
         if dist is not None:
@@ -252,11 +256,18 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         sim.profile(True)
         ev0.record(stream)
-        sim.sweep(args.steps)
+        tail = min(50, args.steps)  # the steady-state part: the last 50 timed sweeps
+        evm = torch.cuda.Event(enable_timing=True)
+        sim.sweep(args.steps - tail)
+        evm.record(stream)
+        sim.sweep(tail)
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
     ms = ev0.elapsed_time(ev1)
+    steady = {"last_sweeps": tail, "value": N * tail / (evm.elapsed_time(ev1) * 1e6),
+              "all_sweeps": args.warmup + args.steps,
+              "value_all": N * (args.warmup + args.steps) / ((warm_ms + ms) * 1e6), "unit": UNIT}
     phase_ms, phase_n = sim.profile_read()
     sim.profile(False)
     ms = max_over_ranks(ms, dist, device="cuda")
@@ -373,6 +384,7 @@ def run_ours(args, rank, world):
         "update_only": {"value": upd, "unit": UNIT, "steps": args.update_only_steps}
         if upd is not None else None,
         "observables_last": {"config": cfg, "E_sat": E, "n": [int(x) for x in n]},
+        "steady_state": steady,
         "batched": batched,
         "xy": xy,
         "wolff": wolff,
