@@ -187,6 +187,32 @@ def cpu_baseline(seconds=15.0, L=8192):
                       f"single-threaded C oracle, {dt:.1f} s"}
 
 
+def _oracle_sample(job):
+    """One process of cpu_baseline_all_cores: seconds for `sweeps` oracle
+    sweeps of an L x L q=2 lattice at T_c."""
+    L, sweeps, seed = job
+    import oracle
+    T = oracle.tc(2)
+    s = oracle.init_spins(L, 2, seed).reshape(-1).copy()
+    t0 = time.perf_counter()
+    oracle.run(L, 2, T, seed, sweeps, spins=s, series=False)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(L=4096, sweeps=6):
+    """The same oracle on every host core at once, one independent lattice
+    per process (replicas are independent, so this is how a CPU would run
+    them): aggregate updates over the slowest process's time."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(n) as pool:
+        times = pool.map(_oracle_sample, [(L, sweeps, 100 + k) for k in range(n)])
+    worst = max(times)
+    return {"value": n * L * L * sweeps / (worst * 1e9), "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"{n} processes, each q=2, T_c, L={L} random start, {sweeps} sweeps; "
+                      f"slowest {worst:.1f} s"}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return 0
@@ -391,6 +417,7 @@ def run_ours(args, rank, world):
     }
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
+        out["cpu_baseline_all_cores"] = cpu_baseline_all_cores()
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
