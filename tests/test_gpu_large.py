@@ -103,3 +103,29 @@ def test_production_size_two_sweeps():
                                                                         [int(x) for x in n1[0]])
     del dev
     torch.cuda.empty_cache()
+
+
+GOLDEN_65536 = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden",
+                                          "l65536_q2_10.json")
+
+
+@pytest.mark.skipif(not __import__("os").path.exists(GOLDEN_65536),
+                    reason="tests/golden/make_l65536_golden.py has not been run")
+def test_production_size_first_ten_sweeps_match_the_oracle_exactly():
+    """The whole L = 65536 lattice, bit for bit: the E_sat and n[s] of the
+    configurations after sweeps 1..10 and the SHA-256 of the spins after
+    sweep 10 equal the oracle's (stored by the golden script)."""
+    import hashlib
+    import json
+
+    g = json.load(open(GOLDEN_65536))
+    assert g["L"] == L and g["q"] == Q and g["seed"] == SEED
+    assert g["thr"] == sw.threshold(sw.tc(Q))
+    with sw.Sim(L, Q, sw.tc(Q), SEED, init="zero", label_bits=64) as s:
+        s.sweep(g["sweeps"])
+        E, n = s.series(1, g["sweeps"])
+        spins = s.spins()
+        s.sync()
+    assert [int(x) for x in E] == g["E"]
+    assert [[int(v) for v in row] for row in n] == g["n"]
+    assert hashlib.sha256(np.ascontiguousarray(spins).tobytes()).hexdigest() == g["spins_sha256"]
