@@ -342,6 +342,12 @@ typedef struct {
  * clamped to 2^32 - 1, into tt[c * (M/2+1) + d] (host array of
  * (M/2+1)^2 entries; M/2 rounded down).  Host only. */
 int sw_xy_thresholds(uint32_t M, double T, uint32_t *tt);
+/* Allocates the lattice (N bytes), the per-site codes (2N), the label
+ * table (4N or 8N bytes, sparse use), per-tile records and the ring through
+ * the installed allocator; uploads the threshold table; measures the
+ * initial configuration (measure = 0).  SW_ERR_INVAL for parameters out of
+ * range (label_bits 32 with L*L > 2^32 included), SW_ERR_NOMEM, SW_ERR_CUDA.
+ * *out is NULL on failure; the handle owns all device memory. */
 int sw_xy_create(const sw_xy_params *prm, sw_xy **out);
 void sw_xy_destroy(sw_xy *xy);
 int sw_xy_bind_stream(sw_xy *xy, void *stream);
@@ -389,6 +395,10 @@ typedef struct sw_wolff sw_wolff;
  * queue of uint32 site indices. */
 int sw_wolff_create(uint64_t L, uint32_t q, double T, uint64_t seed,
                     uint32_t init, uint32_t ring, sw_wolff **out);
+/* (Create: SW_ERR_INVAL for L outside 2..32768, q outside 2..255, T <= 0 or
+ * not finite, a bad init; SW_ERR_NOMEM, SW_ERR_CUDA; *out NULL on failure.
+ * All calls on a handle share its stream; errors from the device are sticky
+ * per handle.) */
 void sw_wolff_destroy(sw_wolff *w);
 int sw_wolff_bind_stream(sw_wolff *w, void *stream);
 /* n steps (asynchronous). */
