@@ -550,11 +550,12 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     if constexpr (kXY) {
       // projection class of every angle on this sweep's embedding axis
       // (Wolff's embedding): sign of sigma in bits 8-9 (1 negative,
-      // 2 positive, 0 zero), fold index c of |sigma| = sin(pi c / M) below
+      // 2 positive, 0 zero), fold index c of |sigma| = sin(pi c / M) below;
+      // built for the CTA's first tile only (one lattice, one sweep)
       uint16_t* xcls = reinterpret_cast<uint16_t*>(sobs);
       const uint32_t M = b.M;
-      const uint32_t jx = pick_state(stream4_rk(b.rk, 0ull, sweep, kDomAxis).x, M);
-      for (uint32_t k = tid; k < M; k += kThreads) {
+      const uint32_t jx = it == 0 ? pick_state(stream4_rk(b.rk, 0ull, sweep, kDomAxis).x, M) : 0u;
+      for (uint32_t k = tid; it == 0 && k < M; k += kThreads) {
         const uint32_t a = (2 * k >= jx) ? 2 * k - jx : 2 * k + 2 * M - jx;  // (2k - j) mod 2M
         const uint32_t sg = (a == 0 || a == M) ? 0u : (a < M ? 1u : 2u);
         const uint32_t bm = a >= M ? a - M : a;
@@ -912,7 +913,12 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     }
     if (tid < R::kBitWords) b.ebits[(uint64_t)t * R::kBitWords + tid] = cbits[tid];
     __syncthreads();  // smem is reused by the next tile
-    if (Src::kMulti && measure) flush(b, q_states);  // each tile may belong to another replica
+    // a replica's observables go out when the CTA's next tile belongs to
+    // another replica (or there is none); until then they accumulate
+    if (Src::kMulti && measure) {
+      const uint32_t gn = g + gridDim.x;
+      if (gn >= total || src.rep(gn) != rep) flush(b, q_states);
+    }
   }
 
   // ---- observables of the configuration read (Sec. 4), once per CTA
