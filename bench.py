@@ -335,15 +335,14 @@ def run_ours(args, rank, world):
         del dev_tmp
         torch.cuda.empty_cache()
         hnp = host.numpy()
-        sim.set_spins(hnp)
-        sim.sweep(1)
-        sim.measure()
+        sim.sweep_host(hnp, 1)
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            sim.set_spins(hnp)
-            sim.sweep(1)
-            sim.measure()
+            # one public call per step: upload from page-locked memory (in
+            # bands, overlapped with the labelling), one sweep, observables
+            # back to the host
+            sim.sweep_host(hnp, 1)
         dt = time.perf_counter() - t0
         e2e = {"value": N * args.e2e_steps * world / (dt * 1e9), "unit": UNIT,
                "h2d_bytes_per_step": N, "d2h_bytes_per_step": 8 * (2 + q),

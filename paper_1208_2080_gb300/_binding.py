@@ -30,7 +30,7 @@ EXPORTS = [
     "sw_set_allocator", "sw_create", "sw_create_ex", "sw_destroy", "sw_bind_stream", "sw_sweep",
     "sw_measure", "sw_series", "sw_spins", "sw_set_spins", "sw_bonds", "sw_get_sweep",
     "sw_set_sweep", "sw_sync", "sw_info", "sw_threshold", "sw_label_bonds", "sw_strerror",
-    "sw_last_error", "sw_profile", "sw_profile_read",
+    "sw_last_error", "sw_profile", "sw_profile_read", "sw_sweep_host",
     "sw_batch_create", "sw_batch_create_ex", "sw_batch_destroy", "sw_batch_bind_stream",
     "sw_batch_sweep", "sw_batch_measure", "sw_batch_series", "sw_batch_spins",
     "sw_batch_set_spins", "sw_batch_get_sweep", "sw_batch_sync", "sw_batch_info",
@@ -126,6 +126,7 @@ def lib():
         "sw_get_sweep": (i32, [vp, u64p]),
         "sw_set_sweep": (i32, [vp, u64]),
         "sw_sync": (i32, [vp]),
+        "sw_sweep_host": (i32, [vp, vp, u64, u64, ctypes.POINTER(sw_obs)]),
         "sw_info": (i32, [vp, ctypes.POINTER(sw_info_t)]),
         "sw_threshold": (i32, [ctypes.c_double, ctypes.POINTER(ctypes.c_uint32)]),
         "sw_label_bonds": (i32, [u64, vp, vp, u32, u32, vp]),
@@ -332,6 +333,16 @@ class Sim:
         a = np.ascontiguousarray(np.asarray(src, dtype=np.uint8).reshape(-1))
         check(lib().sw_set_spins(self._h, a.ctypes.data_as(ctypes.c_void_p), self.N, 0),
               "sw_set_spins")
+
+    def sweep_host(self, src, nsweeps=1):
+        """Upload a host configuration (numpy uint8, L*L; page-locked memory
+        overlaps the upload with the first sweep), run nsweeps sweeps and
+        return (E_sat, n[q], configuration index) of the result."""
+        a = np.ascontiguousarray(np.asarray(src, dtype=np.uint8).reshape(-1))
+        o = sw_obs()
+        check(lib().sw_sweep_host(self._h, a.ctypes.data_as(ctypes.c_void_p), self.N, int(nsweeps),
+                                  ctypes.byref(o)), "sw_sweep_host")
+        return int(o.E_sat), np.array(o.n[: self.q], dtype=np.uint64), int(o.config)
 
     def bonds(self):
         bp = (self.L + 3) // 4

@@ -153,6 +153,8 @@ cudaError_t launch_init(uint8_t* spin, uint64_t N, uint32_t q, uint64_t seed, ui
 }  // namespace swgb
 
 // ------------------------------------------------------------------ handle
+constexpr uint32_t kUploadBands = 16;  // sw_sweep_host: bands of tile rows
+
 struct sw_sim {
   sw_params p;
   uint64_t L = 0, N = 0;
@@ -175,6 +177,9 @@ struct sw_sim {
   std::vector<cudaEvent_t> ev_pool;   // free events
   std::vector<cudaEvent_t> ev_used;   // 4 per profiled sweep, in order
   double prof_ms[3] = {0, 0, 0};
+  // sw_sweep_host: upload stream and one event per band (created on first use)
+  cudaStream_t up = nullptr;
+  cudaEvent_t up_ev[kUploadBands + 1] = {};
   uint64_t prof_launches[3] = {0, 0, 0};
 };
 
@@ -235,6 +240,10 @@ int drain_events(sw_sim* s) {
 }
 
 void release_all(sw_sim* s) {
+  for (cudaEvent_t& e : s->up_ev)
+    if (e) cudaEventDestroy(e), e = nullptr;
+  if (s->up) cudaStreamDestroy(s->up);
+  s->up = nullptr;
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   for (cudaEvent_t e : s->ev_used) cudaEventDestroy(e);
   s->ev_pool.clear();
@@ -263,6 +272,39 @@ int measure_current(sw_sim* s) {
   if (e != cudaSuccess) return cuda_fail(s, e);
   s->pending = false;
   return SW_OK;
+}
+
+// One sweep whose labelling runs band by band: band b of tile rows starts
+// as soon as its rows and the first row of band b+1 (its halo) have been
+// uploaded (events ev[] recorded on the upload stream).  The labelling of a
+// band also checks every spin it reads (BandSrc).
+template <int TH, typename LabelT>
+cudaError_t sweep_banded(sw_sim* s, uint32_t rows_per, uint32_t nb) {
+  const Lattice& lat = s->lat;
+  cudaError_t e;
+  for (uint32_t bnd = 0; bnd < nb; ++bnd) {
+    const uint32_t r0 = bnd * rows_per;
+    const uint32_t r1 = r0 + rows_per < lat.nty ? r0 + rows_per : lat.nty;
+    const uint32_t nxt = (bnd + 1) % nb;
+    if ((e = cudaStreamWaitEvent(s->stream, s->up_ev[bnd], 0))) return e;
+    if (nxt != bnd && (e = cudaStreamWaitEvent(s->stream, s->up_ev[nxt], 0))) return e;
+    const BandSrc src{s->b, lat, r0 * lat.ntx, (r1 - r0) * lat.ntx};
+    if ((e = launch_label_src<TH, LabelT, false, false>(src, (r1 - r0) * lat.ntx, s->stream))) return e;
+  }
+  const SingleSrc full{s->b, lat};
+  if ((e = launch_merge_src<TH, LabelT>(full, lat.ntiles, s->stream))) return e;
+  if ((e = launch_resolve_src<TH, LabelT>(full, lat.ntiles, s->stream))) return e;
+  return launch_recolor_src<TH, LabelT, false>(full, lat.ntiles, (LabelT*)nullptr, s->stream);
+}
+
+template <typename LabelT>
+cudaError_t sweep_banded_th(sw_sim* s, uint32_t rows_per, uint32_t nb) {
+  switch (s->th) {
+    case 16: return sweep_banded<16, LabelT>(s, rows_per, nb);
+    case 32: return sweep_banded<32, LabelT>(s, rows_per, nb);
+    case 64: return sweep_banded<64, LabelT>(s, rows_per, nb);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -544,6 +586,61 @@ int sw_set_spins(sw_sim* s, const uint8_t* src, uint64_t n, int src_on_device) {
   }
   s->spins_invalid = false;
   return SW_OK;
+}
+
+int sw_sweep_host(sw_sim* s, const uint8_t* src, uint64_t n, uint64_t nsweeps, sw_obs* out) {
+  if (!s || !src || n != s->N || nsweeps == 0) return SW_ERR_INVAL;
+  if (sticky(s)) return s->last_err;
+  cudaError_t e = cudaSuccess;
+  if (!s->up) {
+    e = cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking);
+    for (uint32_t k = 0; !e && k <= kUploadBands; ++k)
+      e = cudaEventCreateWithFlags(&s->up_ev[k], cudaEventDisableTiming);
+    if (e) return cuda_fail(s, e);
+  }
+  const Lattice& lat = s->lat;
+  const uint32_t rows_per = (lat.nty + kUploadBands - 1) / kUploadBands;
+  const uint32_t nb = (lat.nty + rows_per - 1) / rows_per;
+  // the upload may only overwrite the spins once earlier work on them is done
+  e = cudaEventRecord(s->up_ev[kUploadBands], s->stream);
+  if (!e) e = cudaStreamWaitEvent(s->up, s->up_ev[kUploadBands], 0);
+  for (uint32_t bnd = 0; !e && bnd < nb; ++bnd) {
+    const uint64_t y0 = (uint64_t)bnd * rows_per * s->th;
+    uint64_t y1 = (uint64_t)(bnd + 1) * rows_per * s->th;
+    if (y1 > s->L) y1 = s->L;
+    e = cudaMemcpyAsync(s->b.spin + y0 * s->L, src + y0 * s->L, (y1 - y0) * s->L, cudaMemcpyHostToDevice,
+                        s->up);
+    if (!e) e = cudaEventRecord(s->up_ev[bnd], s->up);
+  }
+  if (!e)
+    e = s->label_bits == 64 ? sweep_banded_th<uint64_t>(s, rows_per, nb)
+                            : sweep_banded_th<uint32_t>(s, rows_per, nb);
+  if (e) return cuda_fail(s, e);
+  // the uploaded configuration is configuration `sweep`, measured by the
+  // labelling of its first sweep
+  s->measured_from = s->sweep;
+  s->spins_invalid = false;
+  s->sweep += 1;
+  s->pending = true;
+  if (nsweeps > 1) {
+    int rc = sw_sweep(s, nsweeps - 1);
+    if (rc) return rc;
+  }
+  // a spin >= q read by the banded labelling: the configuration was invalid
+  uint32_t err = 0;
+  e = cudaMemcpyAsync(&err, s->b.err, 4, cudaMemcpyDeviceToHost, s->stream);
+  if (!e) e = cudaStreamSynchronize(s->stream);
+  if (e) return cuda_fail(s, e);
+  if (err & kErrSpin) {
+    const uint32_t rest = err & ~kErrSpin;
+    e = cudaMemcpyAsync(s->b.err, &rest, 4, cudaMemcpyHostToDevice, s->stream);
+    if (!e) e = cudaStreamSynchronize(s->stream);
+    if (e) return cuda_fail(s, e);
+    s->spins_invalid = true;
+    return SW_ERR_INVAL;
+  }
+  if (out) return sw_measure(s, out);
+  return check_device(s);
 }
 
 int sw_profile(sw_sim* s, int enable) {

@@ -59,7 +59,9 @@ constexpr uint32_t kFindCap = 1u << 24;   // bound on any global union-find walk
 constexpr uint32_t kLocalCap = 1u << 16;  // bound on any shared-memory walk
 constexpr int kMergeThreads = 256;
 
-enum : uint32_t { kErrFind = 1u, kErrUnion = 2u, kErrLocal = 4u };
+// kErrSpin: a spin >= q was read by a labelling that checks its input
+// (BandSrc); the host reports it as an invalid configuration.
+enum : uint32_t { kErrFind = 1u, kErrUnion = 2u, kErrLocal = 4u, kErrSpin = 8u };
 
 __host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
 
@@ -162,6 +164,7 @@ struct SingleSrc {
   Bufs b;
   Lattice lat;
   static constexpr bool kMulti = false;
+  static constexpr bool kCheck = false;
   __device__ __forceinline__ uint32_t ntiles() const { return lat.ntiles; }
   __device__ __forceinline__ uint32_t rep(uint32_t) const { return 0; }
   __device__ __forceinline__ const Bufs& bufs(uint32_t) const { return b; }
@@ -175,11 +178,28 @@ struct BatchSrc {
   uint32_t total;                         // tiles of all replicas
   uint32_t nrep;
   static constexpr bool kMulti = true;
+  static constexpr bool kCheck = false;
   __device__ __forceinline__ uint32_t ntiles() const { return total; }
   __device__ __forceinline__ uint32_t rep(uint32_t g) const { return __ldg(tile_rep + g); }
   __device__ __forceinline__ const Bufs& bufs(uint32_t r) const { return reps[r].b; }
   __device__ __forceinline__ const Lattice& lattice(uint32_t r) const { return reps[r].lat; }
   __device__ __forceinline__ uint32_t tile0(uint32_t r) const { return reps[r].tile0; }
+};
+
+// BandSrc: tiles base .. base+count-1 of one lattice (whole tile rows), for
+// a labelling that starts while later rows are still being uploaded; it
+// also checks that every spin it reads is < q (kErrSpin).
+struct BandSrc {
+  Bufs b;
+  Lattice lat;
+  uint32_t base, count;
+  static constexpr bool kMulti = false;
+  static constexpr bool kCheck = true;
+  __device__ __forceinline__ uint32_t ntiles() const { return count; }
+  __device__ __forceinline__ uint32_t rep(uint32_t) const { return 0; }
+  __device__ __forceinline__ const Bufs& bufs(uint32_t) const { return b; }
+  __device__ __forceinline__ const Lattice& lattice(uint32_t) const { return lat; }
+  __device__ __forceinline__ uint32_t tile0(uint32_t) const { return 0u - base; }  // t = g + base
 };
 
 __device__ __forceinline__ void tile_geom(const Lattice& lat, uint32_t t, int TH, uint64_t& x0,
@@ -424,7 +444,7 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
   const int lx0 = 4 * lane;
   uint16_t* q = wq + warp * kTW;
   const uint32_t total = src.ntiles();
-  uint32_t bad = 0;
+  uint32_t bad = 0, spin_bad = 0;
 
   for (int k = tid; k < 257; k += kThreads) sobs[k] = 0;
   uint32_t* xtt = reinterpret_cast<uint32_t*>(smem + S::kXYTab);  // XY form only
@@ -589,6 +609,11 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         }
       } else {
         const uint32_t s = *reinterpret_cast<const uint32_t*>(spc + ly * kSpPitch + lx0);
+        if constexpr (Src::kCheck) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (((vm >> k) & 1u) && ((s >> (8 * k)) & 0xFFu) >= q_states) spin_bad = 1u;
+        }
         const uint32_t sn = *reinterpret_cast<const uint32_t*>(spc + ly * kSpPitch + lx0 + 4);
         const uint32_t sd = *reinterpret_cast<const uint32_t*>(spc + (ly + 1) * kSpPitch + lx0);
         const uint32_t sr = __funnelshift_r(s, sn, 8);
@@ -927,6 +952,7 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     if (b0.measure) flush(b0, b0.q);
   }
   if (bad) atomicOr(src.bufs(0).err, kErrLocal);
+  if (spin_bad) atomicOr(src.bufs(0).err, kErrSpin);
 }
 
 // ================================================================== k_merge

@@ -303,3 +303,49 @@ def test_set_spins_from_page_locked_host_memory(L):
         pinned[0] = 7
         with pytest.raises(sw.SwError):
             s.set_spins(pinned.numpy())
+
+
+@pytest.mark.parametrize("L,tile_h", [(5, 0), (64, 16), (130, 32), (1000, 64), (2048, 64)])
+def test_sweep_host_overlapped_upload_matches_oracle(L, tile_h):
+    """sw_sweep_host: banded upload + labelling from a host configuration
+    (pageable and page-locked) gives the oracle's chain and observables."""
+    import torch
+    q, seed = 3, 40 + L
+    T = sw.tc(q)
+    s0 = oracle.init_spins(L, q, seed + 1)
+    ref, E, n = oracle.run(L, q, T, seed, 3, spins=s0, sweep0=2)
+    with sw.Sim(L, q, T, seed, tile_h=tile_h) as s:
+        s.sweep(2)
+        Eg, ng, cfg = s.sweep_host(s0, 3)
+        assert cfg == 5
+        assert Eg == int(E[-1]) and np.array_equal(ng, n[-1])
+        assert np.array_equal(s.spins(), ref)
+        Es, ns = s.series(2, 4)  # the uploaded configuration and the three after it
+        assert int(Es[0]) == oracle.measure(s0, q)[0]
+        assert np.array_equal(Es[1:], E) and np.array_equal(ns[1:], n)
+        pinned = torch.from_numpy(s0.reshape(-1).copy()).pin_memory()
+        ref2, E2, _ = oracle.run(L, q, T, seed, 1, spins=s0, sweep0=5)
+        Eg2, _, cfg2 = s.sweep_host(pinned.numpy(), 1)
+        assert cfg2 == 6 and Eg2 == int(E2[-1])
+        assert np.array_equal(s.spins(), ref2)
+        s.sync()
+
+
+def test_sweep_host_rejects_an_invalid_configuration():
+    L, q = 96, 2
+    with sw.Sim(L, q, sw.tc(q), 3) as s:
+        bad = oracle.init_spins(L, q, 9)
+        bad[50, 17] = 2
+        with pytest.raises(sw.SwError) as e:
+            s.sweep_host(bad, 1)
+        assert e.value.code == -1
+        with pytest.raises(sw.SwError) as e:
+            s.sweep(1)
+        assert e.value.code == -5
+        good = oracle.init_spins(L, q, 9)
+        s.set_spins(good)
+        cur = s.sweep_count
+        s.sweep(2)
+        ref, _, _ = oracle.run(L, q, sw.tc(q), 3, 2, spins=good, sweep0=cur)
+        assert np.array_equal(s.spins(), ref)
+        s.sync()
