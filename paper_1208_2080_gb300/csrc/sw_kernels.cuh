@@ -356,11 +356,29 @@ __device__ __forceinline__ LabelT find_global(LabelT* T, LabelT x, uint32_t* err
   return x;
 }
 
+// find_global with the first parent p = T[x] already loaded.
+template <typename LabelT>
+__device__ __forceinline__ LabelT find_global_from(LabelT* T, LabelT x, LabelT p, uint32_t* err) {
+  for (uint32_t it = 0; it < kFindCap; ++it) {
+    if (p == x) return x;
+    const LabelT gp = ldcg(T + p);
+    if (gp == p) return p;
+    T[x] = gp;
+    x = gp;
+    p = ldcg(T + x);
+  }
+  atomicOr(err, kErrFind);
+  return x;
+}
+
 template <typename LabelT>
 __device__ __forceinline__ void unite_global(LabelT* T, LabelT a, LabelT b, uint32_t* err) {
   for (uint32_t it = 0; it < kFindCap; ++it) {
-    a = find_global(T, a, err);
-    b = find_global(T, b, err);
+    // both first parents in flight at once: the common case (two roots, or
+    // one step from them) costs one round trip instead of two
+    const LabelT pa = ldcg(T + a), pb = ldcg(T + b);
+    a = find_global_from(T, a, pa, err);
+    b = find_global_from(T, b, pb, err);
     if (a == b) return;
     if (a < b) {
       const LabelT tmp = a;
