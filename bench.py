@@ -571,7 +571,7 @@ def main():
     ap.add_argument("--label-bits", type=int, default=0, help="0 = auto (64 above L=32768)")
     ap.add_argument("--tile-h", type=int, default=0, help="labelling tile height (0 = auto)")
     ap.add_argument("--ref-L", type=int, default=4096, help="oracle sample size per reference step")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--update-only-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-R", type=int, default=512, help="replicas in the batched measurement")
