@@ -338,15 +338,19 @@ def run_ours(args, rank, world):
         sim.sweep_host(hnp, 1)
         barrier()
         t0 = time.perf_counter()
+        step_ms = []
         for _ in range(args.e2e_steps):
             # one public call per step: upload from page-locked memory (in
             # bands, overlapped with the labelling), one sweep, observables
             # back to the host
+            ts = time.perf_counter()
             sim.sweep_host(hnp, 1)
+            step_ms.append((time.perf_counter() - ts) * 1e3)
         dt = time.perf_counter() - t0
         e2e = {"value": N * args.e2e_steps * world / (dt * 1e9), "unit": UNIT,
                "h2d_bytes_per_step": N, "d2h_bytes_per_step": 8 * (2 + q),
-               "steps": args.e2e_steps}
+               "steps": args.e2e_steps, "step_ms_min": min(step_ms),
+               "step_ms_median": sorted(step_ms)[len(step_ms) // 2]}
 
     batched = None
     if args.batch_sweeps > 0:
