@@ -6,7 +6,7 @@ observables of a batch of SW runs, the map (q, log2 L, T/T_c) ->
 (u, <|m|>, log chi, U4).  It is used only to decide WHERE to measure: for a
 new (q, L) it predicts chi(T) on a fine grid and places the next temperature
 grid around the predicted peak.  It never touches the Markov chain; the
-measured sweeps at the placed temperatures are the judge of its error, and
+measured sweeps at the placed temperatures decide its error, and
 the plain uniform grid on [0.9, 1.1] T_c is the fallback and the comparison.
 
 Observables of one run (configurations after a 10% burn-in), with
