@@ -129,3 +129,28 @@ def test_production_size_first_ten_sweeps_match_the_oracle_exactly():
     assert [int(x) for x in E] == g["E"]
     assert [[int(v) for v in row] for row in n] == g["n"]
     assert hashlib.sha256(np.ascontiguousarray(spins).tobytes()).hexdigest() == g["spins_sha256"]
+
+
+@pytest.mark.skipif(not __import__("os").path.exists(GOLDEN_65536),
+                    reason="tests/golden/make_l65536_golden.py has not been run")
+def test_production_size_from_host_with_banded_upload_matches_the_oracle():
+    """The same ten sweeps started through sw_sweep_host (the all-zero
+    configuration uploaded from page-locked host memory in bands, the first
+    sweep's labelling overlapped with the upload): the same chain."""
+    import hashlib
+    import json
+
+    import torch
+
+    g = json.load(open(GOLDEN_65536))
+    host = torch.zeros(L * L, dtype=torch.uint8).pin_memory()
+    with sw.Sim(L, Q, sw.tc(Q), SEED, init="random", label_bits=64) as s:
+        E_last, n_last, cfg = s.sweep_host(host.numpy(), g["sweeps"])
+        assert cfg == g["sweeps"]
+        assert E_last == g["E"][-1] and [int(x) for x in n_last] == g["n"][-1]
+        E, n = s.series(1, g["sweeps"])
+        spins = s.spins()
+        s.sync()
+    assert [int(x) for x in E] == g["E"]
+    assert [[int(v) for v in row] for row in n] == g["n"]
+    assert hashlib.sha256(np.ascontiguousarray(spins).tobytes()).hexdigest() == g["spins_sha256"]
