@@ -1040,6 +1040,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__
     }
     b.ctl[1] = s;
     b.ctl[0] = s + 1ull;
+    // XY form: the sweep's embedding axis, for the reflections
+    if (b.M) b.ctl[2] = pick_state(stream4_rk(b.rk, 0ull, (uint32_t)s, kDomAxis).x, b.M);
   }
 }
 
@@ -1096,10 +1098,7 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const __grid_constant__ Sr
   const uint16_t* ol = b.olist + (uint64_t)t * R::kOpenCap;
   uint32_t jx = 0, Mx = 0;
   if constexpr (kXY) {
-    __shared__ uint32_t s_axis;
-    if (tid == 0) s_axis = pick_state(stream4_rk(b.rk, 0ull, (uint32_t)b.ctl[1], kDomAxis).x, b.M);
-    __syncthreads();
-    jx = s_axis;
+    jx = (uint32_t)b.ctl[2];  // the sweep's embedding axis, filed by k_merge
     Mx = b.M;
   }
   // new spin of a site with old spin k whose cluster drew st
