@@ -781,7 +781,8 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         link_rows(ly, rowbits[rr] & 0xFu, (rowbits[rr] >> 4) & 0xFu, rb, pb);
       }
     }
-    __syncthreads();
+    // no barrier: the lock-free unions are order independent, so a warp may
+    // link across the block boundary while its neighbour still links inside
     {
       const int ly = warp * kRpw + kRpw - 1;
       if (warp + 1 < kWarps && ly < h - 1) {  // warp-uniform
