@@ -570,10 +570,12 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     tile_geom(lat, t, TH, x0, y0, w, h);
     uint8_t* spc = sp + (it & 1u) * S::kSpBuf;  // this tile's staged spins
     if (tid < R::kBitWords) cbits[tid] = 0;
+    bool synced = false;  // a barrier already separates this tile from the last one
     if (!kGiven) {
       if (pre) {
         cp_async_wait();
         __syncthreads();  // every thread's copies of this tile have landed
+        synced = true;
       } else {
         stage(g, spc, false);
       }
@@ -601,7 +603,9 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
       }
     }
     if (tid == 0) nsites += (uint32_t)(w * h);
-    __syncthreads();
+    // synchronous staging, the zeroed cross bits (labelling from given
+    // bonds) or the XY class table must be visible before the bonds pass
+    if (!synced || (kXY && it == 0)) __syncthreads();
 
     // ---- bonds, measurement, horizontal runs
     uint32_t rowbits[kRpw];  // bits 0-3 internal right, 4-7 internal down, 8-11 run starts
@@ -956,7 +960,9 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
       }
     }
     if (tid < R::kBitWords) b.ebits[(uint64_t)t * R::kBitWords + tid] = cbits[tid];
-    __syncthreads();  // smem is reused by the next tile
+    // no barrier here: the next tile touches shared memory that this tile
+    // still reads (P, root lists) only after its own first barrier, and the
+    // cross bits only through the threads that read them here
     // a replica's observables go out when the CTA's next tile belongs to
     // another replica (or there is none); until then they accumulate
     if (Src::kMulti && measure) {
