@@ -422,7 +422,8 @@ __device__ __forceinline__ uint32_t byte_mask(uint32_t nib) {
 
 // ================================================================== k_label_tile
 // Persistent: CTA c labels tiles c, c + gridDim.x, ...; while it works on one
-// tile the next tile's spin rows are already in flight into registers.
+// tile the next tile's spin rows are already in flight into the second
+// shared staging buffer (cp.async).
 //
 // kGiven: bonds are read from b.bonds instead of drawn (labelling-only entry).
 // kRoots: closed clusters keep their local root in the code (no new state).
