@@ -454,8 +454,10 @@ typedef struct sw_mlp sw_mlp;
 int sw_mlp_create(const float *init, sw_mlp **out);
 void sw_mlp_destroy(sw_mlp *mlp);
 int sw_mlp_bind_stream(sw_mlp *mlp, void *stream);
-/* Y = f(X) for B rows (device pointers; asynchronous). */
+/* Y = f(X) for B rows (device pointers; asynchronous).  sw_mlp_predict is
+ * the same call under the name used for inference. */
 int sw_mlp_forward(sw_mlp *mlp, const float *X, uint32_t B, float *Y);
+int sw_mlp_predict(sw_mlp *mlp, const float *X, uint32_t B, float *Y);
 /* Gradient of loss = sum(mask*(f(X)-Yt)^2)/(4B) (mask NULL = all ones) into
  * grad (device, SW_MLP_PARAMS floats) and the loss into *loss (device, may be
  * NULL); the rounding is treated as the identity in the backward pass. */

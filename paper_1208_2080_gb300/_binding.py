@@ -37,7 +37,7 @@ EXPORTS = [
     "sw_batch_profile", "sw_batch_profile_read", "sw_batch_last_error", "sw_label_bonds_static",
     "sw_mlp_create", "sw_mlp_destroy", "sw_mlp_bind_stream", "sw_mlp_forward", "sw_mlp_gradients",
     "sw_mlp_train_step", "sw_mlp_get_params", "sw_mlp_set_params", "sw_label_bonds_le",
-    "sw_label_bonds_2stage",
+    "sw_label_bonds_2stage", "sw_mlp_predict",
     "sw_xy_thresholds", "sw_xy_create", "sw_xy_destroy", "sw_xy_bind_stream", "sw_xy_sweep",
     "sw_xy_sync", "sw_xy_series", "sw_xy_spins", "sw_xy_set_spins", "sw_xy_get_sweep",
     "sw_xy_profile", "sw_xy_profile_read", "sw_xy_last_error",
@@ -155,6 +155,7 @@ def lib():
         "sw_mlp_destroy": (None, [vp]),
         "sw_mlp_bind_stream": (i32, [vp, vp]),
         "sw_mlp_forward": (i32, [vp, vp, u32, vp]),
+        "sw_mlp_predict": (i32, [vp, vp, u32, vp]),
         "sw_mlp_gradients": (i32, [vp, vp, vp, vp, u32, vp, vp]),
         "sw_mlp_train_step": (i32, [vp, vp, vp, vp, u32, ctypes.c_float, vp]),
         "sw_mlp_get_params": (i32, [vp, vp, vp]),
@@ -712,6 +713,9 @@ class Mlp:
 
     def forward(self, X, Y):
         check(lib().sw_mlp_forward(self._h, self._p(X), X.shape[0], self._p(Y)), "sw_mlp_forward")
+
+    def predict(self, X, Y):
+        check(lib().sw_mlp_predict(self._h, self._p(X), X.shape[0], self._p(Y)), "sw_mlp_predict")
 
     def gradients(self, X, Yt, mask, grad, loss=None):
         check(lib().sw_mlp_gradients(self._h, self._p(X), self._p(Yt), self._p(mask), X.shape[0],

@@ -363,6 +363,8 @@ int sw_mlp_forward(sw_mlp* h, const float* X, uint32_t B, float* Y) {
   return run_forward(h, X, B, nullptr, Y);
 }
 
+int sw_mlp_predict(sw_mlp* h, const float* X, uint32_t B, float* Y) { return sw_mlp_forward(h, X, B, Y); }
+
 int sw_mlp_gradients(sw_mlp* h, const float* X, const float* Tg, const float* mask, uint32_t B,
                      float* grad, float* loss) {
   if (!h || !X || !Tg || !grad || B == 0) return SW_ERR_INVAL;

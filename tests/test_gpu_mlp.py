@@ -109,3 +109,18 @@ def test_surrogate_grid_finds_the_peak_and_resolves_it():
     assert c["grid_spacing_over_Tc"]["surrogate"] * 3 < c["grid_spacing_over_Tc"]["uniform"]
     assert c["points_above_half_max"]["surrogate"] >= 3 * c["points_above_half_max"]["uniform"]
     model.close()
+
+
+def test_predict_is_forward():
+    import torch
+    rng = np.random.default_rng(5)
+    init = rng.uniform(-0.3, 0.3, omlp.N_PARAMS).astype(np.float32)
+    X = torch.tensor(rng.uniform(-1, 1, (64, 3)), dtype=torch.float32, device="cuda")
+    Y1 = torch.empty((64, 4), dtype=torch.float32, device="cuda")
+    Y2 = torch.empty_like(Y1)
+    m = sw.Mlp(init)
+    m.forward(X, Y1)
+    m.predict(X, Y2)
+    torch.cuda.synchronize()
+    m.close()
+    assert torch.equal(Y1, Y2)
