@@ -7,10 +7,10 @@
  *   (1) bond activation between equal nearest-neighbour spins with
  *       probability p = 1 - exp(-1/T)                       (Sec. 2, step 1)
  *   (2) connected-component labelling of the bond graph; a cluster's label
- *       is its smallest site index, the Hoshen-Kopelman "proper label"
+ *       is its smallest site index, the Hoshen-Kopelman label          
  *                                                          (Sec. 2, step 2)
  *   (3) a uniformly random new state per cluster           (Sec. 2, step 3)
- *   (4) integer energy / magnetisation reductions ("update + measurement",
+ *   (4) integer energy / magnetisation reductions (update plus measurement,
  *       Sec. 4, Table 1).
  *
  * Conventions (shared with the CPU oracle so every configuration is
@@ -93,7 +93,7 @@ typedef struct {
   uint32_t store_bonds; /* 1 = keep the packed bond lattice of the latest
                            sweep (sw_bonds); costs 0.25 B/site per sweep */
   uint32_t measure;     /* 0 = default (on); 2 = off: sweeps record no
-                           observables ("update only", Sec. 4 Table 1) */
+                           observables (update only, Sec. 4 Table 1) */
   uint32_t reserved[3];
 } sw_params;
 

@@ -6,7 +6,7 @@ It wraps the plain C oracle in ``sw_oracle.c`` (conventions in
 ``sw_oracle.h``) with numpy arrays; it shares no code with the CUDA path.
 
 Every function follows Sec. 2 of Komura & Okabe (Eq. 1 and the three SW
-steps); measurement follows Sec. 4 (Table 1, "update + measurement").
+steps); measurement follows Sec. 4 (Table 1, update plus measurement).
 
 The ``wolff_*`` functions wrap ``wolff_oracle.c``: the Wolff single-cluster
 update of the related work (Sec. 1), pinned in tests/test_oracle_wolff.py.

@@ -54,8 +54,8 @@ static uint32_t stream_word(uint64_t seed, uint64_t idx, uint32_t sweep,
 enum { DOM_BOND = 0, DOM_SPIN = 1, DOM_INIT = 2 };
 
 /* Bond probability p = 1 - exp(-J/T), J = 1 (the standard SW probability
- * for H = -J sum delta; the paper only says "depending upon the
- * temperature", Sec. 2 step (1)). */
+ * for H = -J sum delta; Sec. 2 step (1) gives no formula, only that the
+ * activation depends on the temperature). */
 uint32_t orc_threshold(double T) {
   double p = -expm1(-1.0 / T);
   double t = floor(p * 4294967296.0);
@@ -64,7 +64,7 @@ uint32_t orc_threshold(double T) {
   return (uint32_t)t;
 }
 
-/* Sec. 2 step (3): "set randomly to one of q". */
+/* Sec. 2 step (3): a uniformly random one of the q states. */
 uint32_t orc_pick(uint32_t w, uint32_t q) {
   return (uint32_t)(((uint64_t)w * q) >> 32);
 }

@@ -11,12 +11,12 @@
  * algorithm for the simulation of two-dimensional q-state Potts model",
  * Sec. 2, Eq. 1 and the three SW steps that follow it):
  *   (1) bonds between nearest-neighbour sites are activated depending on T,
- *   (2) the active bonds partition the lattice into clusters, labelled with
- *       the Hoshen-Kopelman rule "the proper label of a cluster is the
- *       smallest label of any spin in it",
+ *   (2) the active bonds partition the lattice into clusters, labelled after
+ *       Hoshen and Kopelman: a cluster's label is the smallest label of
+ *       its sites,
  *   (3) every cluster is set to one of the q states uniformly at random.
- * Measurement of energy and magnetisation follows Sec. 4 (Table 1's
- * "update + measurement" mode).
+ * Measurement of energy and magnetisation follows Sec. 4 (the update plus
+ * measurement column of Table 1).
  *
  * Conventions fixed here (the paper is silent on them; both sides follow
  * them so the GPU path must reproduce every configuration bit for bit):
@@ -33,7 +33,7 @@
  *       spins  : ctr = (lo(r),    hi(r),    sweep, 1), word 0, r = root
  *       init   : ctr = (lo(i>>2), hi(i>>2), 0,     2), word i&3
  *   - a 32-bit word w picks state floor(w*q / 2^32).
- *   - the root of a cluster is its minimum site index (HK "proper label").
+ *   - the root of a cluster is its minimum site index (the Hoshen-Kopelman label).
  *   - E_sat = number of satisfied bonds (0..2N); n[s] = sites in state s.
  */
 #ifndef SW_ORACLE_H

@@ -36,7 +36,7 @@
 //
 // Union always links the larger root under the smaller one, so the final
 // root of every cluster is its smallest site index -- the Hoshen-Kopelman
-// "proper label" of Sec. 2 -- independent of the order in which the GPU
+// label of Sec. 2 -- independent of the order in which the GPU
 // happens to process unions.  That makes the result bit-exact with the
 // sequential oracle.  Every union-find walk is bounded (kFindCap); a walk
 // that hits the bound sets an error bit and stops instead of spinning.

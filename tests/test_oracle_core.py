@@ -73,7 +73,7 @@ def test_measure_matches_brute_force_counts():
             assert list(n) == [int((s == k).sum()) for k in range(q)]
 
 
-# ---- labelling (Sec. 2 step (2), HK "proper label" = smallest) --------------
+# ---- labelling (Sec. 2 step (2), Hoshen-Kopelman label = smallest) ---------
 
 def _random_bonds(rng, L, density):
     b = (rng.random((L, L)) < density).astype(np.uint8) * exact.RIGHT
