@@ -1235,49 +1235,30 @@ static __global__ void __launch_bounds__(256) k_measure(const uint8_t* s, Lattic
   const uint32_t qs = q <= 8 ? q - 1 : 0;
   uint32_t e = 0, cnt[7] = {0, 0, 0, 0, 0, 0, 0}, nsites = 0;
   if ((L & 15u) == 0) {
-    // a band of consecutive rows per block, 16-site groups of a row over
-    // threads (16 B loads); walking down the band, a row read as the lower
-    // neighbour is kept in registers as the next row, so each row is read
-    // from memory once (plus one row per band)
+    // rows over blocks, 16-site groups of a row over threads (16 B loads)
     const uint64_t g16 = L >> 4;
-    const uint64_t rows = (L + gridDim.x - 1) / gridDim.x;
-    const uint64_t ya = (uint64_t)blockIdx.x * rows;
-    const uint64_t yb = ya + rows < L ? ya + rows : L;
-    auto count16 = [&](const uint4& v, const uint4& d, uint32_t nx) {
-      const uint32_t w4[5] = {v.x, v.y, v.z, v.w, nx};
-      const uint32_t d4[4] = {d.x, d.y, d.z, d.w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint32_t r = __funnelshift_r(w4[k], w4[k + 1], 8);
-        e += __popc(zero_bytes4(w4[k] ^ r)) + __popc(zero_bytes4(w4[k] ^ d4[k]));
-        if (qs) {
-#pragma unroll
-          for (uint32_t st = 0; st < 7; ++st)
-            if (st < qs) cnt[st] += __popc(zero_bytes4(w4[k] ^ (st * 0x01010101u)));
-        } else {
-          for (int j = 0; j < 4; ++j) atomicAdd(&hist[1 + ((w4[k] >> (8 * j)) & 0xFFu)], 1u);
-        }
-      }
-      nsites += 16;
-    };
-    for (uint64_t gx = threadIdx.x; ya < yb && gx < g16; gx += blockDim.x) {
-      const uint64_t x = gx * 16, xn = (x + 16 == L) ? 0 : x + 16;
-      uint4 v = *reinterpret_cast<const uint4*>(s + ya * L + x);
-      uint64_t y = ya;
-      for (; y + 1 < yb; y += 2) {  // two rows per step: both lower rows in flight
-        const uint64_t y1 = y + 1, y2 = (y + 2 == L) ? 0 : y + 2;
-        const uint4 d1 = *reinterpret_cast<const uint4*>(s + y1 * L + x);
-        const uint4 d2 = *reinterpret_cast<const uint4*>(s + y2 * L + x);
-        const uint32_t n0 = *reinterpret_cast<const uint32_t*>(s + y * L + xn);
-        const uint32_t n1 = *reinterpret_cast<const uint32_t*>(s + y1 * L + xn);
-        count16(v, d1, n0);
-        count16(d1, d2, n1);
-        v = d2;
-      }
-      if (y < yb) {  // odd band length: the last row
-        const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
+    for (uint64_t y = blockIdx.x; y < L; y += gridDim.x) {
+      const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
+      for (uint64_t gx = threadIdx.x; gx < g16; gx += blockDim.x) {
+        const uint64_t x = gx * 16;
+        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(s + y * L + x));
         const uint4 d = *reinterpret_cast<const uint4*>(s + yd * L + x);
-        count16(v, d, *reinterpret_cast<const uint32_t*>(s + y * L + xn));
+        const uint32_t nx = *reinterpret_cast<const uint32_t*>(s + y * L + ((x + 16 == L) ? 0 : x + 16));
+        const uint32_t w4[5] = {v.x, v.y, v.z, v.w, nx};
+        const uint32_t d4[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t r = __funnelshift_r(w4[k], w4[k + 1], 8);
+          e += __popc(zero_bytes4(w4[k] ^ r)) + __popc(zero_bytes4(w4[k] ^ d4[k]));
+          if (qs) {
+#pragma unroll
+            for (uint32_t st = 0; st < 7; ++st)
+              if (st < qs) cnt[st] += __popc(zero_bytes4(w4[k] ^ (st * 0x01010101u)));
+          } else {
+            for (int j = 0; j < 4; ++j) atomicAdd(&hist[1 + ((w4[k] >> (8 * j)) & 0xFFu)], 1u);
+          }
+        }
+        nsites += 16;
       }
     }
   } else
