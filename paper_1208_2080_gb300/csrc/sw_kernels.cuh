@@ -875,12 +875,23 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         nopen += total >> 16;
       }
     }
+    // ---- new state of each complete cluster, drawn once at its root, by the
+    // warp that listed it (its own rows: no other warp reads these entries
+    // before the next barrier, so this needs no barrier of its own)
+    __syncwarp();
+    if (!kRoots) {
+      for (uint32_t i = lane; i < nclosed; i += 32) {
+        const uint32_t j = wl[i];
+        const uint32_t stt =
+            pick_state(stream4_rk(b.rk, global_index(lat, x0, y0, j), sweep, kDomSpin).x, q_states);
+        P[j] = j | (stt << 16);
+      }
+    }
     if (lane == 0) wcnt[warp] = nclosed | (nopen << 16);
     __syncthreads();
 
-    // ---- new state of each complete cluster, drawn once at its root, by the
-    // warp that listed it; open roots get their slot in the tile's open
-    // list (warp by warp) and a global label
+    // ---- open roots get their slot in the tile's open list (warp by warp)
+    // and a global label
     {
       uint32_t obase = 0, otot = 0;
       if (lane < kWarps) {
@@ -892,14 +903,6 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
       for (int o = 16; o > 0; o >>= 1) {
         obase += __shfl_xor_sync(kFull, obase, o);
         otot += __shfl_xor_sync(kFull, otot, o);
-      }
-      if (!kRoots) {
-        for (uint32_t i = lane; i < nclosed; i += 32) {
-          const uint32_t j = wl[i];
-          const uint32_t stt =
-              pick_state(stream4_rk(b.rk, global_index(lat, x0, y0, j), sweep, kDomSpin).x, q_states);
-          P[j] = j | (stt << 16);
-        }
       }
       for (uint32_t i = lane; i < nopen; i += 32) {
         const uint32_t j = wl[kRegion - 1 - i];
