@@ -798,6 +798,8 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     }
     __syncthreads();
 
+    if (tid == 0) wcnt[0] = 0;  // open-slot counter of this tile
+
     // ---- compress the run starts of the warp's rows (only starts can be
     // roots), and flag clusters that touch the tile edge as open (the edge
     // sites are spread over all threads)
@@ -887,23 +889,13 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         P[j] = j | (stt << 16);
       }
     }
-    if (lane == 0) wcnt[warp] = nclosed | (nopen << 16);
-    __syncthreads();
-
-    // ---- open roots get their slot in the tile's open list (warp by warp)
-    // and a global label
+    // ---- open roots get a block of slots in the tile's open list (in
+    // whatever order the warps arrive: a slot only names the root to later
+    // kernels, results do not depend on it) and a global label
     {
-      uint32_t obase = 0, otot = 0;
-      if (lane < kWarps) {
-        const uint32_t c = wcnt[lane] >> 16;
-        obase = lane < warp ? c : 0u;
-        otot = c;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        obase += __shfl_xor_sync(kFull, obase, o);
-        otot += __shfl_xor_sync(kFull, otot, o);
-      }
+      uint32_t obase = 0;
+      if (lane == 0 && nopen) obase = atomicAdd(&wcnt[0], nopen);
+      obase = __shfl_sync(kFull, obase, 0);
       for (uint32_t i = lane; i < nopen; i += 32) {
         const uint32_t j = wl[kRegion - 1 - i];
         const uint32_t slot = obase + i;
@@ -912,9 +904,9 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         const uint64_t g = global_index(lat, x0, y0, j);
         T[g] = (LabelT)g;
       }
-      if (tid == 0) b.ocnt[t] = otot;
     }
     __syncthreads();
+    if (tid == 0) b.ocnt[t] = wcnt[0];
 
     // ---- per-site codes and the edge lines
     uint16_t* edge = b.edge + (uint64_t)t * R::kEdge;
