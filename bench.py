@@ -11,11 +11,15 @@ measurement).  W warm-up sweeps, then K timed sweeps; with the defaults
 Metric: spin updates per ns = N * K / device time.  The timed region holds
 only the library's kernels (inputs resident in HBM, every buffer far larger
 than the 126 MB L2, so no flush is needed).  `e2e` repeats the metric through
-the public API with host buffers: each step uploads the configuration from
-pinned host memory (sw_set_spins), sweeps once and reads the observables
-back (sw_measure).  `roofline` reports the dominant kernel's achieved HBM
-bandwidth from the library's per-launch CUDA events; `cpu_baseline` times the
-CPU oracle on a bounded sample.
+the public API with host buffers: each step is one sw_sweep_host call, which
+uploads the configuration from pinned host memory (in bands, overlapped with
+the sweep's labelling), sweeps once and reads the observables back.
+`roofline` reports the dominant kernel's achieved HBM bandwidth from the
+library's per-launch CUDA events (and its instruction issue rate);
+`cpu_baseline` times the CPU oracle on a bounded sample, and
+`cpu_baseline_all_cores` the same oracle on every host core.  The line also
+carries the replica batch (`batched`), the XY model (`xy`) and the Wolff
+comparison (`wolff`).
 
 --impl reference times the CPU oracle (the only reference implementation of
 this paper's method) as the reference arm, on rank 0.
