@@ -432,9 +432,11 @@ __device__ __forceinline__ uint32_t byte_mask(uint32_t nib) {
 // (15 bits).  A site that is not the start of its horizontal run keeps
 // pointing at its run start for the whole tile; only run starts take part
 // in unions, so only they are compressed, and every site's root is
-// P[P[j] & kIdx] & kIdx.  Once the root lists are built, a root entry also
-// carries kOpen and, in bits 16..24, its open-root slot (open) or its new
-// state (closed).  Lane l owns sites 4l..4l+3 of a row; its four entries are
+// P[P[j] & kIdx] & kIdx.  An open cluster's root carries kOpen until the
+// root lists are built; then every root entry's high half is the 16-bit
+// site code of its cluster (0x8000|state closed, the open-root slot open;
+// the labelling-only form keeps kOpen on open roots and no state).  Lane l
+// owns sites 4l..4l+3 of a row; its four entries are
 // moved with one 16-byte shared-memory access (conflict free); unions and
 // compressions are compacted into per-warp task queues so that all lanes
 // stay busy.
@@ -886,7 +888,7 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         const uint32_t j = wl[i];
         const uint32_t stt =
             pick_state(stream4_rk(b.rk, global_index(lat, x0, y0, j), sweep, kDomSpin).x, q_states);
-        P[j] = j | (stt << 16);
+        P[j] = j | ((kClosed | stt) << 16);  // the high half is the site code
       }
     }
     // ---- open roots get a block of slots in the tile's open list (in
@@ -900,7 +902,9 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         const uint32_t j = wl[kRegion - 1 - i];
         const uint32_t slot = obase + i;
         b.olist[(uint64_t)t * R::kOpenCap + slot] = (uint16_t)j;
-        P[j] = j | kOpen | (slot << 16);
+        // the high half is the site code (the slot); the labelling-only form
+        // keeps the open flag to tell open from closed roots
+        P[j] = j | (kRoots ? kOpen : 0u) | (slot << 16);
         const uint64_t g = global_index(lat, x0, y0, j);
         T[g] = (LabelT)g;
       }
@@ -928,8 +932,10 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
             pvr = P[pr];
           }
           rt[k] = pr;
-          c[k] = (pvr & kOpen) ? ((pvr >> 16) & 0x1FFu)
-                               : (kRoots ? (kClosed | pr) : (kClosed | ((pvr >> 16) & 0xFFu)));
+          if constexpr (kRoots)
+            c[k] = (pvr & kOpen) ? ((pvr >> 16) & 0x1FFu) : (kClosed | pr);
+          else
+            c[k] = pvr >> 16;
         }
         const uint64_t gi = (y0 + ly) * L + x0 + lx0;
         if (lat.vec4) {
