@@ -922,15 +922,12 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         const uint4 v4 = *reinterpret_cast<const uint4*>(P + rowbase + lx0);
         const uint32_t v[4] = {v4.x, v4.y, v4.z, v4.w};
         uint32_t c[4], rt[4];
-        uint32_t ps = 0xFFFFFFFFu, pr = 0, pvr = 0;
+        // four independent two-step lookups (run start, root), no branches
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const uint32_t x = v[k] & kIdx;  // run start, or the root for a start
-          if (x != ps) {
-            ps = x;
-            pr = P[x] & kIdx;
-            pvr = P[pr];
-          }
+          const uint32_t pr = P[x] & kIdx;
+          const uint32_t pvr = P[pr];
           rt[k] = pr;
           if constexpr (kRoots)
             c[k] = (pvr & kOpen) ? ((pvr >> 16) & 0x1FFu) : (kClosed | pr);
