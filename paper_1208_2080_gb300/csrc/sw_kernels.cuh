@@ -837,47 +837,51 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     // back.
     constexpr int kRegion = kRpw * kTW;
     uint16_t* wl = clist + warp * kRegion;
-    uint32_t nclosed = 0, nopen = 0;  // warp-uniform
+    // a lane's roots over all its rows (bit 4*rr + k), one prefix over the
+    // warp for all rows, then the lane writes its closed and open roots
+    uint32_t cmask = 0, omask = 0;
 #pragma unroll
     for (int rr = 0; rr < kRpw; ++rr) {
       const int ly = warp * kRpw + rr;
-      if (ly < h) {  // warp-uniform
-        const uint32_t rowbase = (uint32_t)(ly * kTW);
-        const uint32_t stb = (rowbits[rr] >> 8) & 0xFu;
-        uint32_t cm = 0, om = 0;
-        if (stb) {
-          const uint4 v4 = *reinterpret_cast<const uint4*>(P + rowbase + lx0);
-          const uint32_t v[4] = {v4.x, v4.y, v4.z, v4.w};
+      const uint32_t stb = (rowbits[rr] >> 8) & 0xFu;
+      if (ly < h && stb) {
+        const uint32_t j0 = (uint32_t)(ly * kTW + lx0);
+        const uint4 v4 = *reinterpret_cast<const uint4*>(P + j0);
+        const uint32_t v[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            if (((stb >> k) & 1u) && (v[k] & kIdx) == rowbase + lx0 + k) {
-              if (v[k] & kOpen) om |= 1u << k; else cm |= 1u << k;
-            }
-          }
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t isroot = ((stb >> k) & 1u) & ((v[k] & kIdx) == j0 + k ? 1u : 0u);
+          const uint32_t open = v[k] >> 31;  // kOpen
+          cmask |= (isroot & (open ^ 1u)) << (4 * rr + k);
+          omask |= (isroot & open) << (4 * rr + k);
         }
-        const uint32_t mine = (uint32_t)__popc(cm) | ((uint32_t)__popc(om) << 16);
-        uint32_t inc = mine;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(kFull, inc, o);
-          if (lane >= o) inc += y;
-        }
-        const uint32_t excl = inc - mine;
-        uint32_t cpos = nclosed + (excl & 0xFFFFu), opos = nopen + (excl >> 16);
-        while (cm) {
-          const int k = __ffs(cm) - 1;
-          cm &= cm - 1u;
-          wl[cpos++] = (uint16_t)(rowbase + lx0 + k);
-        }
-        while (om) {
-          const int k = __ffs(om) - 1;
-          om &= om - 1u;
-          wl[kRegion - 1 - (opos++)] = (uint16_t)(rowbase + lx0 + k);
-        }
-        const uint32_t total = __shfl_sync(kFull, inc, 31);
-        nclosed += total & 0xFFFFu;
-        nopen += total >> 16;
       }
+    }
+    uint32_t nclosed, nopen;  // warp-uniform
+    {
+      const uint32_t mine = (uint32_t)__popc(cmask) | ((uint32_t)__popc(omask) << 16);
+      uint32_t inc = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+      }
+      const uint32_t excl = inc - mine;
+      uint32_t cpos = excl & 0xFFFFu, opos = excl >> 16;
+      const uint32_t jbase = (uint32_t)(warp * kRpw * kTW + lx0);
+      while (cmask) {
+        const int bb = __ffs(cmask) - 1;
+        cmask &= cmask - 1u;
+        wl[cpos++] = (uint16_t)(jbase + (bb >> 2) * kTW + (bb & 3));
+      }
+      while (omask) {
+        const int bb = __ffs(omask) - 1;
+        omask &= omask - 1u;
+        wl[kRegion - 1 - (opos++)] = (uint16_t)(jbase + (bb >> 2) * kTW + (bb & 3));
+      }
+      const uint32_t total = __shfl_sync(kFull, inc, 31);
+      nclosed = total & 0xFFFFu;
+      nopen = total >> 16;
     }
     // ---- new state of each complete cluster, drawn once at its root, by the
     // warp that listed it (its own rows: no other warp reads these entries
