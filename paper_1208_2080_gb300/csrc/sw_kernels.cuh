@@ -803,20 +803,37 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     if (tid == 0) wcnt[0] = 0;  // open-slot counter of this tile
 
     // ---- compress the run starts of the warp's rows (only starts can be
-    // roots), and flag clusters that touch the tile edge as open (the edge
-    // sites are spread over all threads)
+    // roots; all rows in one batch, listed in the root-list area, which is
+    // free until the root lists), and flag clusters that touch the tile
+    // edge as open (the edge sites are spread over all threads)
+    {
+      uint16_t* tq = clist + warp * (kRpw * kTW);
+      const uint32_t jbase = (uint32_t)(warp * kRpw * kTW + lx0);
+      uint32_t smask = 0;
 #pragma unroll
-    for (int rr = 0; rr < kRpw; ++rr) {
-      const int ly = warp * kRpw + rr;
-      if (ly < h) {  // warp-uniform
-        const uint32_t n = warp_enqueue(q, (rowbits[rr] >> 8) & 0xFu, (uint32_t)(ly * kTW), lane);
-        for (uint32_t i = lane; i < n; i += 32) {
-          const uint32_t j = q[i];
-          const uint32_t r = root_masked(P, j, bad);
-          if (r != j) P[j] = r;
-        }
-        __syncwarp();
+      for (int rr = 0; rr < kRpw; ++rr)
+        if (warp * kRpw + rr < h) smask |= ((rowbits[rr] >> 8) & 0xFu) << (4 * rr);
+      const uint32_t mine = (uint32_t)__popc(smask);
+      uint32_t inc = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
       }
+      uint32_t pos = inc - mine;
+      while (smask) {
+        const int bb = __ffs(smask) - 1;
+        smask &= smask - 1u;
+        tq[pos++] = (uint16_t)(jbase + (bb >> 2) * kTW + (bb & 3));
+      }
+      const uint32_t n = __shfl_sync(kFull, inc, 31);
+      __syncwarp();
+      for (uint32_t i = lane; i < n; i += 32) {
+        const uint32_t j = tq[i];
+        const uint32_t r = root_masked(P, j, bad);
+        if (r != j) P[j] = r;
+      }
+      __syncwarp();
     }
     {
       const int nedge = 2 * (w + h);
