@@ -303,22 +303,18 @@ __device__ __forceinline__ uint32_t root_masked(const uint32_t* P, uint32_t x, u
 
 // Warp-level compaction: lane l contributes the sites (4l+k, k in `mask`)
 // of row base `rowbase`; returns the number of tasks written to q[0..n).
+// The tasks are ordered by site k first, then by lane: one ballot per k
+// gives every position without a prefix scan.
 __device__ __forceinline__ uint32_t warp_enqueue(uint16_t* q, uint32_t mask, uint32_t rowbase,
                                                  int lane) {
-  const uint32_t mine = (uint32_t)__popc(mask);
-  uint32_t inc = mine;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t total = 0;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-    if (lane >= o) inc += y;
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t bk = __ballot_sync(0xFFFFFFFFu, (mask >> k) & 1u);
+    if ((mask >> k) & 1u) q[total + __popc(bk & lt)] = (uint16_t)(rowbase + 4 * lane + k);
+    total += __popc(bk);
   }
-  uint32_t pos = inc - mine;
-  while (mask) {
-    const int k = __ffs(mask) - 1;
-    mask &= mask - 1u;
-    q[pos++] = (uint16_t)(rowbase + 4 * lane + k);
-  }
-  const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
   __syncwarp();
   return total;
 }
