@@ -274,22 +274,39 @@ int measure_current(sw_sim* s) {
   return SW_OK;
 }
 
-// One sweep whose labelling runs band by band: band b of tile rows starts
-// as soon as its rows and the first row of band b+1 (its halo) have been
-// uploaded (events ev[] recorded on the upload stream).  The labelling of a
-// band also checks every spin it reads (BandSrc).
+// sw_sweep_host's bands of tile rows: band k is tile rows r[k] .. r[k+1]-1.
+// They start at one tile row and double up to an eighth of the lattice, so
+// that the labelling starts as soon as the first few rows have arrived and
+// the next band's copy (faster than its labelling) keeps ahead of it; the
+// last band takes what is left once kUploadBands bands are planned, or when
+// less than half a band would be left after it.
+uint32_t plan_bands(uint32_t nty, uint32_t* r) {
+  const uint32_t cap = (nty + 7) / 8;
+  uint32_t nb = 0, r0 = 0, sz = 1;
+  while (r0 < nty) {
+    r[nb] = r0;
+    r0 = (nb == kUploadBands - 1 || nty - r0 <= sz + sz / 2) ? nty : r0 + sz;
+    ++nb;
+    sz = 2 * sz < cap ? 2 * sz : cap;
+  }
+  r[nb] = nty;
+  return nb;
+}
+
+// One sweep whose labelling runs band by band: band k starts as soon as the
+// copy of its rows and of its halo row (the first row of band k+1, copied
+// with band k; the last band's halo is row 0, in the first copy) has landed,
+// i.e. on event ev[k] of the upload stream, whose copies complete in order.
+// The labelling of a band also checks every spin it reads (BandSrc).
 template <int TH, typename LabelT>
-cudaError_t sweep_banded(sw_sim* s, uint32_t rows_per, uint32_t nb) {
+cudaError_t sweep_banded(sw_sim* s, const uint32_t* r, uint32_t nb) {
   const Lattice& lat = s->lat;
   cudaError_t e;
   for (uint32_t bnd = 0; bnd < nb; ++bnd) {
-    const uint32_t r0 = bnd * rows_per;
-    const uint32_t r1 = r0 + rows_per < lat.nty ? r0 + rows_per : lat.nty;
-    const uint32_t nxt = (bnd + 1) % nb;
     if ((e = cudaStreamWaitEvent(s->stream, s->up_ev[bnd], 0))) return e;
-    if (nxt != bnd && (e = cudaStreamWaitEvent(s->stream, s->up_ev[nxt], 0))) return e;
-    const BandSrc src{s->b, lat, r0 * lat.ntx, (r1 - r0) * lat.ntx};
-    if ((e = launch_label_src<TH, LabelT, false, false>(src, (r1 - r0) * lat.ntx, s->stream))) return e;
+    const BandSrc src{s->b, lat, r[bnd] * lat.ntx, (r[bnd + 1] - r[bnd]) * lat.ntx};
+    if ((e = launch_label_src<TH, LabelT, false, false>(src, (r[bnd + 1] - r[bnd]) * lat.ntx, s->stream)))
+      return e;
   }
   const SingleSrc full{s->b, lat};
   if ((e = launch_merge_src<TH, LabelT>(full, lat.ntiles, s->stream))) return e;
@@ -298,11 +315,11 @@ cudaError_t sweep_banded(sw_sim* s, uint32_t rows_per, uint32_t nb) {
 }
 
 template <typename LabelT>
-cudaError_t sweep_banded_th(sw_sim* s, uint32_t rows_per, uint32_t nb) {
+cudaError_t sweep_banded_th(sw_sim* s, const uint32_t* r, uint32_t nb) {
   switch (s->th) {
-    case 16: return sweep_banded<16, LabelT>(s, rows_per, nb);
-    case 32: return sweep_banded<32, LabelT>(s, rows_per, nb);
-    case 64: return sweep_banded<64, LabelT>(s, rows_per, nb);
+    case 16: return sweep_banded<16, LabelT>(s, r, nb);
+    case 32: return sweep_banded<32, LabelT>(s, r, nb);
+    case 64: return sweep_banded<64, LabelT>(s, r, nb);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -598,23 +615,25 @@ int sw_sweep_host(sw_sim* s, const uint8_t* src, uint64_t n, uint64_t nsweeps, s
       e = cudaEventCreateWithFlags(&s->up_ev[k], cudaEventDisableTiming);
     if (e) return cuda_fail(s, e);
   }
-  const Lattice& lat = s->lat;
-  const uint32_t rows_per = (lat.nty + kUploadBands - 1) / kUploadBands;
-  const uint32_t nb = (lat.nty + rows_per - 1) / rows_per;
+  uint32_t r[kUploadBands + 1];
+  const uint32_t nb = plan_bands(s->lat.nty, r);
   // the upload may only overwrite the spins once earlier work on them is done
   e = cudaEventRecord(s->up_ev[kUploadBands], s->stream);
   if (!e) e = cudaStreamWaitEvent(s->up, s->up_ev[kUploadBands], 0);
+  // copy k: from the end of copy k-1 through band k's halo row
+  uint64_t y0 = 0;
   for (uint32_t bnd = 0; !e && bnd < nb; ++bnd) {
-    const uint64_t y0 = (uint64_t)bnd * rows_per * s->th;
-    uint64_t y1 = (uint64_t)(bnd + 1) * rows_per * s->th;
+    uint64_t y1 = bnd + 1 < nb ? (uint64_t)r[bnd + 1] * s->th + 1 : s->L;
     if (y1 > s->L) y1 = s->L;
-    e = cudaMemcpyAsync(s->b.spin + y0 * s->L, src + y0 * s->L, (y1 - y0) * s->L, cudaMemcpyHostToDevice,
-                        s->up);
+    if (y1 > y0)
+      e = cudaMemcpyAsync(s->b.spin + y0 * s->L, src + y0 * s->L, (y1 - y0) * s->L, cudaMemcpyHostToDevice,
+                          s->up);
     if (!e) e = cudaEventRecord(s->up_ev[bnd], s->up);
+    y0 = y1;
   }
   if (!e)
-    e = s->label_bits == 64 ? sweep_banded_th<uint64_t>(s, rows_per, nb)
-                            : sweep_banded_th<uint32_t>(s, rows_per, nb);
+    e = s->label_bits == 64 ? sweep_banded_th<uint64_t>(s, r, nb)
+                            : sweep_banded_th<uint32_t>(s, r, nb);
   if (e) return cuda_fail(s, e);
   // the uploaded configuration is configuration `sweep`, measured by the
   // labelling of its first sweep
