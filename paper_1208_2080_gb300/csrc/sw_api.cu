@@ -130,9 +130,18 @@ static cudaError_t label_given_t(uint32_t th, const Bufs& b, const Lattice& lat,
 
 cudaError_t launch_measure(const uint8_t* spin, const Lattice& lat, uint32_t q,
                            const Bufs& b, cudaStream_t st) {
-  uint64_t blocks = lat.L;  // one block per row, at most 16 per SM
-  if (blocks > 152ull * 16) blocks = 152ull * 16;
-  k_measure<<<(unsigned)blocks, 256, 0, st>>>(spin, lat, q, b.acc);
+  if ((lat.L & 15u) == 0) {
+    // column strips of 256 16-site groups x row strips of kMeasRows rows
+    const dim3 grid((unsigned)((lat.L / 16 + 255) / 256), (unsigned)((lat.L + kMeasRows - 1) / kMeasRows));
+    if (q == 2) k_measure16<1><<<grid, 256, 0, st>>>(spin, lat.L, q, b.acc);
+    else if (q <= 4) k_measure16<2><<<grid, 256, 0, st>>>(spin, lat.L, q, b.acc);
+    else if (q <= 8) k_measure16<3><<<grid, 256, 0, st>>>(spin, lat.L, q, b.acc);
+    else k_measure16<0><<<grid, 256, 0, st>>>(spin, lat.L, q, b.acc);
+  } else {
+    uint64_t blocks = lat.L;  // one block per row, at most 16 per SM
+    if (blocks > 152ull * 16) blocks = 152ull * 16;
+    k_measure<<<(unsigned)blocks, 256, 0, st>>>(spin, lat, q, b.acc);
+  }
   cudaError_t e = cudaGetLastError();
   if (e) return e;
   k_commit<<<1, 32, 0, st>>>(b);

@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
   const int lx0 = 4 * lane;
   uint16_t* q = wq + warp * kTW;
   const uint32_t total = src.ntiles();
-  uint32_t bad = 0, spin_bad = 0;
+  uint32_t bad = 0, spin_max = 0;  // spin_max: byte-wise maximum of the spins read (BandSrc)
 
   for (int k = tid; k < 257; k += kThreads) sobs[k] = 0;
   uint32_t* xtt = reinterpret_cast<uint32_t*>(smem + S::kXYTab);  // XY form only
@@ -474,30 +474,31 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
   uint32_t e_loc = 0, nsites = 0;
   uint32_t ncnt[3] = {0, 0, 0};
 
-  // Observables accumulated so far (E_sat, and n[s] for s < q-1 in
-  // registers when q <= 4, else in shared memory) go to the lattice's
-  // accumulator; n[q-1] follows from the site count.  Called by all threads.
+  // Observables accumulated so far (E_sat, and for q <= 4 the bit-plane
+  // counts c1 = n1 + n3, c2 = n2 + n3, c3 = n3 in registers, else n[s] in
+  // shared memory) go to the lattice's accumulator; n[0] follows from the
+  // site count.  Called by all threads.
   auto flush = [&](const Bufs& fb, uint32_t fq) {
-    const uint32_t fqs = fq <= 4 ? fq - 1 : 0;
+    const bool fregs = fq <= 4;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e_loc += __shfl_xor_sync(kFull, e_loc, o);
     if (lane == 0) atomicAdd(&sobs[0], e_loc);
-    if (fqs) {
+    if (fregs) {
 #pragma unroll
-      for (uint32_t st = 0; st < 3; ++st) {
-        if (st < fqs) {
-          uint32_t v = ncnt[st];
+      for (int k = 0; k < 3; ++k)
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-          if (lane == 0) atomicAdd(&sobs[1 + st], v);
-        }
+        for (int o = 16; o > 0; o >>= 1) ncnt[k] += __shfl_xor_sync(kFull, ncnt[k], o);
+      if (lane == 0) {
+        atomicAdd(&sobs[2], ncnt[0] - ncnt[2]);                // n1
+        if (fq > 2) atomicAdd(&sobs[3], ncnt[1] - ncnt[2]);    // n2
+        if (fq > 3) atomicAdd(&sobs[4], ncnt[2]);              // n3
       }
     }
     __syncthreads();
-    if (fqs && tid == 0) {
+    if (fregs && tid == 0) {
       uint32_t rest = nsites;
-      for (uint32_t st = 0; st < fqs; ++st) rest -= sobs[1 + st];
-      sobs[1 + fqs] = rest;
+      for (uint32_t st = 1; st < fq; ++st) rest -= sobs[1 + st];
+      sobs[1] = rest;  // n0
     }
     __syncthreads();
     for (uint32_t k = tid; k <= fq; k += kThreads)
@@ -630,11 +631,7 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         }
       } else {
         const uint32_t s = *reinterpret_cast<const uint32_t*>(spc + ly * kSpPitch + lx0);
-        if constexpr (Src::kCheck) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (((vm >> k) & 1u) && ((s >> (8 * k)) & 0xFFu) >= q_states) spin_bad = 1u;
-        }
+        if constexpr (Src::kCheck) spin_max = __vmaxu4(spin_max, s & byte_mask(vm));
         const uint32_t sn = *reinterpret_cast<const uint32_t*>(spc + ly * kSpPitch + lx0 + 4);
         const uint32_t sd = *reinterpret_cast<const uint32_t*>(spc + (ly + 1) * kSpPitch + lx0);
         const uint32_t sr = __funnelshift_r(s, sn, 8);
@@ -672,9 +669,15 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         if (!kXY && measure) {
           e_loc += __popc(eqr) + __popc(eqd);
           if (qs) {
-#pragma unroll
-            for (uint32_t st = 0; st < 3; ++st)
-              if (st < qs) ncnt[st] += __popc(zero_bytes4(s ^ (st * 0x01010101u)) & vm);
+            // bit planes of the valid sites (q <= 4): bit 0 marks states 1, 3,
+            // bit 1 states 2, 3, both state 3
+            const uint32_t m1 = (vm * 0x00204081u) & 0x01010101u;  // bit 0 of each valid byte
+            ncnt[0] += __popc(s & m1);
+            if (qs > 1) {
+              const uint32_t s1 = (s >> 1) & m1;
+              ncnt[1] += __popc(s1);
+              ncnt[2] += __popc(s & s1);
+            }
           } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
@@ -993,7 +996,10 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     if (b0.measure) flush(b0, b0.q);
   }
   if (bad) atomicOr(src.bufs(0).err, kErrLocal);
-  if (spin_bad) atomicOr(src.bufs(0).err, kErrSpin);
+  if constexpr (Src::kCheck) {
+    const uint32_t m2 = __vmaxu4(spin_max, spin_max >> 16);
+    if ((__vmaxu4(m2, m2 >> 8) & 0xFFu) >= src.bufs(0).q) atomicOr(src.bufs(0).err, kErrSpin);
+  }
 }
 
 // ================================================================== k_merge
@@ -1237,9 +1243,168 @@ static __global__ void k_init_spins(uint8_t* s, uint64_t N, uint32_t q, uint64_t
   }
 }
 
-// E_sat and n[s] of a configuration (the configuration no later sweep reads).
-// One thread per group of 4 sites of a row; 4-byte loads when rows are
-// 4-byte aligned, per-state counts in registers for q <= 8.
+// Block reduction of one thread's measurement counts (E_sat, the states
+// 0 .. qs-1 counted in registers, sites) into hist[] and then acc[]; q > 8
+// (qs = 0) has counted its states in hist[1 + s] already.
+__device__ __forceinline__ void measure_flush(uint32_t* hist, uint32_t e, uint32_t (&cnt)[7],
+                                              uint32_t nsites, uint32_t qs, uint32_t q,
+                                              unsigned long long* acc) {
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
+    nsites += __shfl_xor_sync(0xFFFFFFFFu, nsites, o);
+  }
+  if (qs) {
+#pragma unroll
+    for (uint32_t st = 0; st < 7; ++st)
+      for (int o = 16; o > 0; o >>= 1) cnt[st] += __shfl_xor_sync(0xFFFFFFFFu, cnt[st], o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&hist[0], e);
+    if (qs) {
+      uint32_t rest = nsites;
+      for (uint32_t st = 0; st < qs; ++st) {
+        atomicAdd(&hist[1 + st], cnt[st]);
+        rest -= cnt[st];
+      }
+      atomicAdd(&hist[1 + qs], rest);
+    }
+  }
+  __syncthreads();
+  for (uint32_t k = threadIdx.x; k <= q; k += blockDim.x)
+    if (hist[k]) atomicAdd(&acc[k], (unsigned long long)hist[k]);
+}
+
+// E_sat and n[s] for L a multiple of 16, streaming: thread (gx, strip)
+// holds the 16 sites gx*16 .. gx*16+15 of row y in registers, loads row y+1
+// (its down neighbours, then its own sites of the next step) and takes the
+// right neighbour of its last site from the next lane.  A strip of
+// kMeasRows rows reads each spin once plus one extra row, with kMeasAhead
+// rows' loads in flight per thread.
+//
+// States are counted by bit planes for q <= 2^B (B = 1, 2, 3): c[T-1]
+// counts the sites that have every bit of the plane set T (T = 1 .. 2^B-1)
+// set, and n[s] = sum over T containing s of (-1)^(|T|-|s|) c[T-1]
+// (Moebius inversion over the subsets), n[0] = sites - the rest.  B = 0:
+// q > 8, every site counted in a shared histogram.
+constexpr uint32_t kMeasRows = 64, kMeasAhead = 4;
+template <int B>
+static __global__ void __launch_bounds__(256) k_measure16(const uint8_t* s, uint64_t L, uint32_t q,
+                                                   unsigned long long* acc) {
+  constexpr int NC = B ? (1 << B) - 1 : 1;
+  __shared__ uint32_t hist[257];
+  __shared__ uint32_t bsites;
+  for (int k = threadIdx.x; k < 257; k += blockDim.x) hist[k] = 0;
+  if (threadIdx.x == 0) bsites = 0;
+  __syncthreads();
+  const uint64_t g16 = L >> 4;
+  const uint64_t gx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = gx < g16;
+  const uint64_t x = live ? gx * 16 : 0;
+  const uint64_t xn = (x + 16 == L) ? 0 : x + 16;  // first site of the next group
+  const bool edge = (threadIdx.x & 31) == 31 || gx + 1 >= g16;  // next group not in this warp
+  const uint64_t y0 = (uint64_t)blockIdx.y * kMeasRows;
+  const uint32_t rows = (uint32_t)(L - y0 < kMeasRows ? L - y0 : kMeasRows);
+  uint32_t e = 0, nsites = 0, c[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) c[k] = 0;
+  auto ld = [&](uint64_t y) -> uint4 {
+    const uint64_t yy = y >= L ? y - L : y;
+    return live ? __ldcs(reinterpret_cast<const uint4*>(s + yy * L + x)) : make_uint4(0, 0, 0, 0);
+  };
+  // bit 7 of each byte of the result: that byte of a ^ b is zero
+  auto eq_hi = [](uint32_t a, uint32_t b) -> uint32_t {
+    const uint32_t d = a ^ b;
+    if constexpr (B != 0) return ~(d + 0x7F7F7F7Fu) & 0x80808080u;  // bytes < 128 (q <= 8)
+    else return ~(((d & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | d) & 0x80808080u;
+  };
+  uint4 v = ld(y0);
+  for (uint32_t r = 0; r < rows; r += kMeasAhead) {
+    uint4 nxt[kMeasAhead];
+#pragma unroll
+    for (uint32_t k = 0; k < kMeasAhead; ++k)
+      nxt[k] = (r + k < rows) ? ld(y0 + r + k + 1) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (uint32_t k = 0; k < kMeasAhead; ++k) {
+      if (r + k >= rows) break;  // uniform over the block
+      uint32_t nx = __shfl_down_sync(0xFFFFFFFFu, v.x, 1);
+      if (edge && live) nx = *reinterpret_cast<const uint32_t*>(s + (y0 + r + k) * L + xn);
+      if (live) {
+        const uint32_t w4[5] = {v.x, v.y, v.z, v.w, nx};
+        const uint32_t d4[4] = {nxt[k].x, nxt[k].y, nxt[k].z, nxt[k].w};
+        // the four words' flags packed into disjoint bits, one popcount per
+        // 16 sites: equal right / down neighbours of word j at bits 7-2j and
+        // 6-2j of each byte, plane-set bits of word j at bit j
+        uint32_t eb = 0, pc[NC];
+#pragma unroll
+        for (int t = 0; t < NC; ++t) pc[t] = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t w = w4[j];
+          eb |= (eq_hi(w, __funnelshift_r(w, w4[j + 1], 8)) | (eq_hi(w, d4[j]) >> 1)) >> (2 * j);
+          if constexpr (B == 0) {
+            for (int b = 0; b < 4; ++b) atomicAdd(&hist[1 + ((w >> (8 * b)) & 0xFFu)], 1u);
+          } else {
+            const uint32_t p0 = w & 0x01010101u;
+            pc[0] |= p0 << j;
+            if constexpr (B >= 2) {
+              const uint32_t p1 = (w >> 1) & 0x01010101u;
+              pc[1] |= p1 << j;
+              pc[2] |= (p0 & p1) << j;
+              if constexpr (B == 3) {
+                const uint32_t p2 = (w >> 2) & 0x01010101u;
+                pc[3] |= p2 << j;
+                pc[4] |= (p0 & p2) << j;
+                pc[5] |= (p1 & p2) << j;
+                pc[6] |= (p0 & p1 & p2) << j;
+              }
+            }
+          }
+        }
+        e += __popc(eb);
+        if constexpr (B != 0) {
+#pragma unroll
+          for (int t = 0; t < NC; ++t) c[t] += __popc(pc[t]);
+        }
+        nsites += 16;
+      }
+      v = nxt[k];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
+    nsites += __shfl_xor_sync(0xFFFFFFFFu, nsites, o);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) c[k] += __shfl_xor_sync(0xFFFFFFFFu, c[k], o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&hist[0], e);
+    if constexpr (B != 0) {
+      atomicAdd(&bsites, nsites);
+      for (uint32_t st = 1; st < q; ++st) {
+        int64_t n = 0;
+        for (uint32_t T = st; T < (1u << B); ++T)
+          if ((T & st) == st) n += ((__popc(T) - __popc(st)) & 1) ? -(int64_t)c[T - 1] : (int64_t)c[T - 1];
+        atomicAdd(&hist[1 + st], (uint32_t)n);
+      }
+    }
+  }
+  __syncthreads();
+  if constexpr (B != 0) {
+    if (threadIdx.x == 0) {
+      uint32_t rest = bsites;
+      for (uint32_t st = 1; st < q; ++st) rest -= hist[1 + st];
+      hist[1] = rest;  // n[0]
+    }
+    __syncthreads();
+  }
+  for (uint32_t k = threadIdx.x; k <= q; k += blockDim.x)
+    if (hist[k]) atomicAdd(&acc[k], (unsigned long long)hist[k]);
+}
+
+// E_sat and n[s] of a configuration (the configuration no later sweep reads),
+// any L: one thread per group of 4 sites of a row; 4-byte loads when rows
+// are 4-byte aligned, per-state counts in registers for q <= 8.  Lattices
+// with L a multiple of 16 take k_measure16.
 static __global__ void __launch_bounds__(256) k_measure(const uint8_t* s, Lattice lat, uint32_t q,
                                                  unsigned long long* acc) {
   __shared__ uint32_t hist[257];
@@ -1249,34 +1414,6 @@ static __global__ void __launch_bounds__(256) k_measure(const uint8_t* s, Lattic
   const uint64_t groups = (L + 3) >> 2;
   const uint32_t qs = q <= 8 ? q - 1 : 0;
   uint32_t e = 0, cnt[7] = {0, 0, 0, 0, 0, 0, 0}, nsites = 0;
-  if ((L & 15u) == 0) {
-    // rows over blocks, 16-site groups of a row over threads (16 B loads)
-    const uint64_t g16 = L >> 4;
-    for (uint64_t y = blockIdx.x; y < L; y += gridDim.x) {
-      const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
-      for (uint64_t gx = threadIdx.x; gx < g16; gx += blockDim.x) {
-        const uint64_t x = gx * 16;
-        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(s + y * L + x));
-        const uint4 d = *reinterpret_cast<const uint4*>(s + yd * L + x);
-        const uint32_t nx = *reinterpret_cast<const uint32_t*>(s + y * L + ((x + 16 == L) ? 0 : x + 16));
-        const uint32_t w4[5] = {v.x, v.y, v.z, v.w, nx};
-        const uint32_t d4[4] = {d.x, d.y, d.z, d.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint32_t r = __funnelshift_r(w4[k], w4[k + 1], 8);
-          e += __popc(zero_bytes4(w4[k] ^ r)) + __popc(zero_bytes4(w4[k] ^ d4[k]));
-          if (qs) {
-#pragma unroll
-            for (uint32_t st = 0; st < 7; ++st)
-              if (st < qs) cnt[st] += __popc(zero_bytes4(w4[k] ^ (st * 0x01010101u)));
-          } else {
-            for (int j = 0; j < 4; ++j) atomicAdd(&hist[1 + ((w4[k] >> (8 * j)) & 0xFFu)], 1u);
-          }
-        }
-        nsites += 16;
-      }
-    }
-  } else
   // rows over blocks, 4-site groups of a row over threads
   for (uint64_t y = blockIdx.x; y < L; y += gridDim.x) {
     const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
@@ -1313,29 +1450,7 @@ static __global__ void __launch_bounds__(256) k_measure(const uint8_t* s, Lattic
       }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
-    nsites += __shfl_xor_sync(0xFFFFFFFFu, nsites, o);
-  }
-  if (qs) {
-#pragma unroll
-    for (uint32_t st = 0; st < 7; ++st)
-      for (int o = 16; o > 0; o >>= 1) cnt[st] += __shfl_xor_sync(0xFFFFFFFFu, cnt[st], o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&hist[0], e);
-    if (qs) {
-      uint32_t rest = nsites;
-      for (uint32_t st = 0; st < qs; ++st) {
-        atomicAdd(&hist[1 + st], cnt[st]);
-        rest -= cnt[st];
-      }
-      atomicAdd(&hist[1 + qs], rest);
-    }
-  }
-  __syncthreads();
-  for (uint32_t k = threadIdx.x; k <= q; k += blockDim.x)
-    if (hist[k]) atomicAdd(&acc[k], (unsigned long long)hist[k]);
+  measure_flush(hist, e, cnt, nsites, qs, q, acc);
 }
 
 // Sets *bad if any of the N spins is >= q (validation of a new configuration).

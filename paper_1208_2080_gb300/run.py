@@ -1,6 +1,7 @@
 """Run one workload of the library on the GPU and print a JSON summary.
 
     python -m paper_1208_2080_gb300.run potts --L 16384 --q 2 --sweeps 5
+    python -m paper_1208_2080_gb300.run potts --L 65536 --sweeps 3 --host
     python -m paper_1208_2080_gb300.run xy --L 16384 --M 256 --sweeps 5
     python -m paper_1208_2080_gb300.run wolff --L 4096 --q 2 --steps 10 --mode label
 
@@ -25,6 +26,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--label-bits", type=int, default=0)
     ap.add_argument("--mode", default="label", choices=["label", "grow"])
+    ap.add_argument("--host", action="store_true")
     a = ap.parse_args()
 
     import torch
@@ -36,10 +38,17 @@ def main():
     if a.model == "potts":
         T = sw.tc(a.q) if a.T is None else a.T
         with sw.Sim(a.L, a.q, T, a.seed, init="zero", label_bits=a.label_bits) as s:
-            e0.record(stream)
-            s.sweep(a.sweeps)
-            e1.record(stream)
-            E, n, cfg = s.measure()
+            if a.host:
+                host = torch.zeros(N, dtype=torch.uint8).pin_memory().numpy()
+                e0.record(stream)
+                for _ in range(a.sweeps):
+                    E, n, cfg = s.sweep_host(host, 1)
+                e1.record(stream)
+            else:
+                e0.record(stream)
+                s.sweep(a.sweeps)
+                e1.record(stream)
+                E, n, cfg = s.measure()
             s.sync()
         out = {"E_sat": E, "n": [int(x) for x in n], "config": cfg}
         work = N * a.sweeps

@@ -153,6 +153,22 @@ def test_zero_start_and_resume():
         assert np.array_equal(b.spins(), end)
 
 
+@pytest.mark.parametrize("L", [16, 48, 80, 130, 1040, 4112])
+@pytest.mark.parametrize("q", [2, 3, 8, 9, 40])
+def test_measure_of_a_given_configuration(L, q):
+    """sw_measure of an uploaded configuration (k_measure16 for L a multiple
+    of 16: strips of 64 rows with a short last strip at L = 1040 and 4112,
+    a second, nearly empty column chunk at L = 4112; the per-row kernel at
+    L = 130; register counts for q <= 8, shared histograms above)."""
+    rng = np.random.default_rng(7 * L + q)
+    s0 = rng.integers(0, q, size=(L, L), dtype=np.uint8)
+    E, n = oracle.measure(s0, q)
+    with sw.Sim(L, q, sw.tc(q), 5) as s:
+        s.set_spins(s0)
+        Eg, ng, _ = s.measure()
+    assert Eg == int(E) and np.array_equal(ng, np.asarray(n, dtype=np.uint64))
+
+
 def test_measurement_off_gives_same_chain():
     L, q, T, seed = 140, 3, sw.tc(3), 11
     with sw.Sim(L, q, T, seed) as a, sw.Sim(L, q, T, seed, measure=False) as b:
