@@ -111,17 +111,19 @@ GOLDEN_65536 = __import__("os").path.join(__import__("os").path.dirname(__file__
 
 @pytest.mark.skipif(not __import__("os").path.exists(GOLDEN_65536),
                     reason="tests/golden/make_l65536_golden.py has not been run")
-def test_production_size_first_ten_sweeps_match_the_oracle_exactly():
+@pytest.mark.parametrize("label_bits", [64, 32])
+def test_production_size_first_ten_sweeps_match_the_oracle_exactly(label_bits):
     """The whole L = 65536 lattice, bit for bit: the E_sat and n[s] of the
     configurations after sweeps 1..10 and the SHA-256 of the spins after
-    sweep 10 equal the oracle's (stored by the golden script)."""
+    sweep 10 equal the oracle's (stored by the golden script).  With 32-bit
+    labels the N = 2^32 site indices use the whole label range."""
     import hashlib
     import json
 
     g = json.load(open(GOLDEN_65536))
     assert g["L"] == L and g["q"] == Q and g["seed"] == SEED
     assert g["thr"] == sw.threshold(sw.tc(Q))
-    with sw.Sim(L, Q, sw.tc(Q), SEED, init="zero", label_bits=64) as s:
+    with sw.Sim(L, Q, sw.tc(Q), SEED, init="zero", label_bits=label_bits) as s:
         s.sweep(g["sweeps"])
         E, n = s.series(1, g["sweeps"])
         spins = s.spins()
