@@ -149,21 +149,24 @@ int sw_set_spins(sw_sim *sim, const uint8_t *src, uint64_t n,
  * equal L*ceil(L/4).  Requires store_bonds = 1. */
 int sw_bonds(sw_sim *sim, uint8_t *dst, uint64_t nbytes, int dst_on_device);
 
-/* Sweep counter (the Philox "sweep" counter word of the next sweep); with
- * the spins it is the whole state of a run, so get + spins, then set +
- * set_spins, resumes a run bit for bit. */
 /* One call from a host configuration to observables: uploads the N spins
- * from `src` (host memory; page-locked memory lets the upload overlap) in
- * up to 16 bands of tile rows on a stream of the handle's own, runs `nsweeps`
- * sweeps of which the first labels each band as soon as that band and its
- * halo row have arrived, and, if `out` is not NULL, fills it as
- * sw_measure.  The uploaded configuration becomes configuration `sweep`
+ * from `src` (host memory; page-locked memory lets the upload overlap) on a
+ * stream of the handle's own in at most 16 bands of tile rows (one tile row
+ * first, then doubling up to an eighth of the lattice, each copy carrying
+ * its band's halo row), runs `nsweeps` sweeps of which the first labels
+ * each band as soon as its copy has landed, and, if `out` is not NULL,
+ * fills it as sw_measure (the observables of the resulting
+ * configuration).  The uploaded configuration becomes configuration `sweep`
  * (as after sw_set_spins).  The banded labelling checks every spin: a spin
  * >= q gives SW_ERR_INVAL after the call, the lattice is then undefined and
  * sweeps return SW_ERR_STATE until a valid configuration is set.  Not
  * recorded by sw_profile.  Synchronises the handle's stream. */
 int sw_sweep_host(sw_sim *sim, const uint8_t *src, uint64_t n,
                   uint64_t nsweeps, sw_obs *out);
+
+/* Sweep counter (the Philox "sweep" counter word of the next sweep); with
+ * the spins it is the whole state of a run, so get + spins, then set +
+ * set_spins, resumes a run bit for bit. */
 int sw_get_sweep(const sw_sim *sim, uint64_t *sweep);
 int sw_set_sweep(sw_sim *sim, uint64_t sweep);
 
