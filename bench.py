@@ -393,6 +393,22 @@ def run_ours(args, rank, world):
             "frac": achieved / peak, "peak_kind": peak_kind, "traffic": _traffic(name, L),
             "alg_bytes_per_launch": alg, "avg_launch_ms": avg[dom],
             "phase_ms_per_sweep": {PHASES[k]: avg[k] for k in range(3)}}
+    # every phase's algorithmic HBM rate, and the whole sweep's (6 B/site:
+    # spin read + code write in the labelling, code read + spin write in the
+    # recolour; the merge and resolve touch only sparse tile records)
+    phases = {}
+    for k, pname in enumerate(PHASES):
+        pb = ALG_BYTES_PER_SITE[pname] * N
+        rate = pb / (avg[k] * 1e-3) / 1e9 if avg[k] > 0 and pb > 0 else None
+        phases[pname] = {"ms": avg[k], "alg_bytes": pb, "GB/s": rate,
+                         "frac": rate / peak if rate is not None else None}
+    sweep_bytes = sum(ALG_BYTES_PER_SITE.values()) * N
+    sweep_ms = sum(avg)
+    roof["phases"] = phases
+    roof["sweep"] = {"ms": sweep_ms, "alg_bytes": sweep_bytes,
+                     "GB/s": sweep_bytes / (sweep_ms * 1e-3) / 1e9 if sweep_ms > 0 else None}
+    if roof["sweep"]["GB/s"] is not None:
+        roof["sweep"]["frac"] = roof["sweep"]["GB/s"] / peak
     # the tile kernel is bound by instruction issue, not by HBM: its issue
     # rate against the GPU's issue peak (instruction count per site from ncu)
     winst = _profile_figure(name, "warp_inst_per_site", L)
