@@ -40,6 +40,8 @@ def lib():
         u64p = ctypes.POINTER(ctypes.c_uint64)
         L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
         L.orc_philox4x32_10.restype = None
+        L.orc_philox_many.argtypes = [ctypes.c_uint64, u32p, u32p]
+        L.orc_philox_many.restype = None
         L.orc_threshold.argtypes = [ctypes.c_double]
         L.orc_threshold.restype = ctypes.c_uint32
         L.orc_pick.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
@@ -103,6 +105,15 @@ def philox(ctr, key):
     out = np.zeros(4, dtype=np.uint32)
     lib().orc_philox4x32_10(_p(c, ctypes.c_uint32), _p(k, ctypes.c_uint32),
                             _p(out, ctypes.c_uint32))
+    return out
+
+
+def philox_many(inp):
+    """Philox4x32-10 of every row of an (n, 6) uint32 array (counter words,
+    then key words) -> (n, 4) uint32, one oracle call per row."""
+    a = np.ascontiguousarray(np.asarray(inp, dtype=np.uint32).reshape(-1, 6))
+    out = np.zeros((a.shape[0], 4), dtype=np.uint32)
+    lib().orc_philox_many(a.shape[0], _p(a, ctypes.c_uint32), _p(out, ctypes.c_uint32))
     return out
 
 

@@ -41,6 +41,10 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+void orc_philox_many(uint64_t n, const uint32_t *in, uint32_t *out) {
+  for (uint64_t i = 0; i < n; ++i) orc_philox4x32_10(in + 6 * i, in + 6 * i + 4, out + 4 * i);
+}
+
 /* Philox word `word` for stream (seed; idx, sweep, domain). */
 static uint32_t stream_word(uint64_t seed, uint64_t idx, uint32_t sweep,
                             uint32_t domain, int word) {

@@ -50,6 +50,10 @@ enum { ORC_RIGHT = 1, ORC_DOWN = 2 };
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
                        uint32_t out[4]);
 
+/* The same for n inputs: in[6i .. 6i+3] counter, in[6i+4 .. 6i+5] key,
+ * out[4i .. 4i+3] the words (one call per input, for tests). */
+void orc_philox_many(uint64_t n, const uint32_t *in, uint32_t *out);
+
 /* Integer bond threshold floor((1 - exp(-1/T)) * 2^32), clamped. */
 uint32_t orc_threshold(double T);
 

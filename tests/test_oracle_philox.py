@@ -90,3 +90,16 @@ def test_avalanche_and_uniformity():
     e = len(words) / 256
     chi2 = ((cnt - e) ** 2 / e).sum()
     assert chi2 < 255 + 6 * np.sqrt(2 * 255)
+
+
+def test_batched_form_equals_single_calls():
+    """oracle.philox_many (the batched entry the GPU Philox test uses) gives
+    the single-call oracle's words row by row, including the all-zero and
+    all-ones counters."""
+    rng = np.random.default_rng(11)
+    inp = rng.integers(0, 2 ** 32, size=(500, 6), dtype=np.uint64).astype(np.uint32)
+    inp[0] = 0
+    inp[1, :4] = 0xFFFFFFFF
+    got = oracle.philox_many(inp)
+    for i in range(inp.shape[0]):
+        assert list(got[i]) == list(oracle.philox(inp[i, :4], inp[i, 4:]))
