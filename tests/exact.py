@@ -10,6 +10,10 @@
 * ``sw_transition``    -- the exact SW transition matrix of a tiny lattice,
                           built from a caller-supplied labeller, for the
                           stationarity / detailed-balance checks.
+* ``kaufman_mean_esat`` -- exact <E_sat> of q = 2 on an L x L torus of any
+                          size from Kaufman's closed-form partition function
+                          of the periodic Ising lattice (as written by
+                          Ferdinand and Fisher, Phys. Rev. 185, 832 (1969)).
 """
 from collections import deque
 import itertools
@@ -242,3 +246,43 @@ def wolff_transition(L, q, p):
                     s2 = np.where(comp, new, s)
                     P[si, int(s2 @ powers)] += w / (q - 1)
     return P, E
+
+
+def kaufman_logz(K, m, n):
+    """ln Z of the Ising model sum exp(K * sum_<ij> s_i s_j) on an m x n
+    periodic lattice (mpmath number):
+      Z = 1/2 (2 sinh 2K)^(mn/2) (Z1 + Z2 + Z3 + Z4),
+      Z1 = prod_{r<n} 2 cosh(m g_{2r+1}/2),  Z2 = prod 2 sinh(m g_{2r+1}/2),
+      Z3 = prod_{r<n} 2 cosh(m g_{2r}/2),    Z4 = prod 2 sinh(m g_{2r}/2),
+    with cosh g_l = cosh 2K coth 2K - cos(pi l / n) for l > 0 and
+    g_0 = 2K + ln tanh K (negative below T_c, which makes Z4 change sign)."""
+    import mpmath as mp
+    K = mp.mpf(K)
+    c = mp.cosh(2 * K) * mp.coth(2 * K)
+
+    def g(l):
+        if l == 0:
+            return 2 * K + mp.log(mp.tanh(K))
+        return mp.acosh(c - mp.cos(mp.pi * l / n))
+
+    z1 = z2 = z3 = z4 = mp.mpf(1)
+    for r in range(n):
+        a, b = m * g(2 * r + 1) / 2, m * g(2 * r) / 2
+        z1 *= 2 * mp.cosh(a)
+        z2 *= 2 * mp.sinh(a)
+        z3 *= 2 * mp.cosh(b)
+        z4 *= 2 * mp.sinh(b)
+    return mp.log(mp.mpf(1) / 2) + (m * n / mp.mpf(2)) * mp.log(2 * mp.sinh(2 * K)) + \
+        mp.log(z1 + z2 + z3 + z4)
+
+
+def kaufman_mean_esat(L, T):
+    """Exact <E_sat> of the q = 2 Potts model at temperature T on an L x L
+    torus (L >= 3): with delta = (1 + s s')/2 the Potts weight exp(E_sat/T)
+    is the Ising weight at K = 1/(2T) times exp(N/T), so
+    <E_sat> = N + (1/2) d ln Z / dK."""
+    import mpmath as mp
+    mp.mp.dps = 50
+    K = mp.mpf(1) / (2 * mp.mpf(T))
+    d = mp.diff(lambda k: kaufman_logz(k, L, L), K)
+    return float(L * L + d / 2)

@@ -1,6 +1,7 @@
 """Statistical pins of the whole oracle chain (RNG keying, bond rule, labelling,
 recolouring together) against exact results it does not compute:
-brute-force enumeration, transfer matrices and Baxter's closed form for the
+brute-force enumeration, transfer matrices, Kaufman's closed-form partition
+function of the finite Ising torus, and Baxter's closed form for the
 critical energy, u(T_c) = -(1 + 1/sqrt q)."""
 import numpy as np
 import pytest
@@ -106,3 +107,37 @@ def test_3x3_ising_state_histogram_chi_square():
     chi2 = ((counts - expect) ** 2 / expect).sum()
     dof = m - 1
     assert chi2 < dof + 6 * np.sqrt(2 * dof), (chi2, dof)
+
+
+def test_kaufman_closed_form_matches_enumeration_and_transfer_matrix():
+    """The closed form itself, before it judges the chain: equal to the
+    4 x 4 enumeration and the 6 x 6 transfer matrix at four temperatures
+    either side of T_c."""
+    for T in [oracle.tc(2), 0.8 * oracle.tc(2), 1.5 * oracle.tc(2), 3.0]:
+        b1, _, _ = exact.brute_moments(4, 2, T)
+        assert abs(exact.kaufman_mean_esat(4, T) - b1) < 1e-9 * b1
+        t1, _ = exact.transfer_moments(6, 6, 2, T)
+        assert abs(exact.kaufman_mean_esat(6, T) - t1) < 1e-7 * t1
+
+
+@pytest.mark.parametrize("L,f,n", [(32, 1.0, 40_000), (64, 1.0, 12_000), (32, 0.9, 20_000),
+                                   (32, 1.2, 20_000)])
+def test_ising_torus_energy_matches_kaufman(L, f, n):
+    """<E_sat> of the q = 2 chain on the L = 32 and 64 tori at T_c and either
+    side of it equals Kaufman's exact finite-size value within 5 sigma (no
+    finite-size allowance needed, unlike the Baxter check)."""
+    T = f * oracle.tc(2)
+    ref = exact.kaufman_mean_esat(L, T)
+    E, _ = _chain(L, 2, T, seed=7000 + L + int(100 * f), n=n)
+    m, s = _batch_mean(E)
+    assert abs(m - ref) < 5 * s, (m, ref, s)
+
+
+def test_kaufman_check_catches_a_one_percent_temperature_error():
+    """The same L = 32 check rejects a chain run 1% off T_c, the size of
+    error a slightly wrong bond probability would make."""
+    T = oracle.tc(2)
+    ref = exact.kaufman_mean_esat(32, T)
+    E, _ = _chain(32, 2, 1.01 * T, seed=7100, n=40_000)
+    m, s = _batch_mean(E)
+    assert abs(m - ref) > 5 * s, (m, ref, s)
