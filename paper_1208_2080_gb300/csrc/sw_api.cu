@@ -70,6 +70,7 @@ Lattice make_lattice(uint64_t L, uint32_t th) {
   lat.bp = (L + 3) / 4;
   lat.vec4 = (L % 4 == 0) ? 1u : 0u;
   lat.ntiles = lat.ntx * lat.nty;
+  lat.ntx_m = lat.ntx == 1 ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / lat.ntx);
   return lat;
 }
 

@@ -51,7 +51,7 @@ namespace swgb {
 constexpr int kTW = 128;                  // tile width (32 lanes x 4 sites)
 constexpr int kThreads = 512;             // threads per tile CTA
 constexpr int kWarps = kThreads / 32;
-constexpr int kSpPitch = 132;             // smem spin row: 128 sites, halo, pad
+constexpr int kSpPitch = 144;             // smem spin row: 128 sites, halo; 16-byte rows
 constexpr uint32_t kOpen = 0x80000000u;   // smem root flag: cluster touches tile edge
 constexpr uint32_t kIdx = 0x7FFFu;        // local index bits
 constexpr uint16_t kClosed = 0x8000u;     // code flag: cluster complete in tile
@@ -110,6 +110,7 @@ struct Lattice {
   uint64_t bp;        // packed-bond row pitch in bytes, ceil(L/4)
   uint32_t vec4;      // L % 4 == 0: rows start 4-byte aligned
   uint32_t ntiles;
+  uint32_t ntx_m;     // floor(2^32 / ntx) (2^32 - 1 for ntx = 1): t / ntx by a multiply
 };
 
 struct Bufs {
@@ -202,9 +203,24 @@ struct BandSrc {
   __device__ __forceinline__ uint32_t tile0(uint32_t) const { return 0u - base; }  // t = g + base
 };
 
+// Tile column and row of tile t: the quotient by ntx from a multiply-high by
+// floor(2^32 / ntx), which is the true quotient or one less for every 32-bit
+// t, and one correction step.
+__device__ __forceinline__ void tile_xy(const Lattice& lat, uint32_t t, uint32_t& tx, uint32_t& ty) {
+  uint32_t qt = __umulhi(t, lat.ntx_m);
+  uint32_t rt = t - qt * lat.ntx;
+  if (rt >= lat.ntx) {
+    ++qt;
+    rt -= lat.ntx;
+  }
+  tx = rt;
+  ty = qt;
+}
+
 __device__ __forceinline__ void tile_geom(const Lattice& lat, uint32_t t, int TH, uint64_t& x0,
                                           uint64_t& y0, int& w, int& h) {
-  const uint32_t tx = t % lat.ntx, ty = t / lat.ntx;
+  uint32_t tx, ty;
+  tile_xy(lat, t, tx, ty);
   x0 = (uint64_t)tx * kTW;
   y0 = (uint64_t)ty * TH;
   const uint64_t rw = lat.L - x0, rh = lat.L - y0;
@@ -398,6 +414,11 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
+// 16-byte asynchronous global -> shared copy, both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -513,7 +534,8 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
   // ---- stage a tile's spin rows (0..h-1 and the halo row h) plus each
   // row's halo byte at column w into a shared buffer.  Rows start 4-byte
   // aligned when L % 4 == 0: then the copies are asynchronous (cp.async)
-  // and the next tile is staged while this one is labelled.
+  // and the next tile is staged while this one is labelled; 16 bytes per
+  // copy (8 lanes a row, 4 rows a warp) when L % 16 == 0.
   auto stage = [&](uint32_t gg, uint8_t* buf, bool async) {
     const uint32_t fr = src.rep(gg);
     const Lattice& fl = src.lattice(fr);
@@ -525,6 +547,20 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     // halo row and column wrap around the lattice (x0 + w <= L, y0 + h <= L)
     const uint64_t hx = (fx0 + fw == FL) ? 0 : fx0 + fw;
     const uint64_t hy = (fy0 + fh == FL) ? 0 : fy0 + fh;
+    if (async && (FL & 15u) == 0 && (reinterpret_cast<uintptr_t>(fspin) & 15u) == 0) {
+      // w is a multiple of 16 here (x0 a multiple of 128, L of 16)
+      const int c16 = (lane & 7) * 16;
+      for (int ly = warp * 4 + (lane >> 3); ly <= fh; ly += 4 * kWarps) {
+        const uint64_t gy = (ly < fh) ? (fy0 + ly) : hy;
+        if (c16 < fw) cp_async16(buf + ly * kSpPitch + c16, fspin + gy * FL + fx0 + c16);
+      }
+      // halo column: 4 aligned bytes starting at column (x0 + w) mod L
+      for (int ly = tid; ly <= fh; ly += kThreads) {
+        const uint64_t gy = (ly < fh) ? (fy0 + ly) : hy;
+        cp_async4(buf + ly * kSpPitch + fw, fspin + gy * FL + hx);
+      }
+      return;
+    }
     for (int ly = warp; ly <= fh; ly += kWarps) {
       const uint64_t gy = (ly < fh) ? (fy0 + ly) : hy;
       const uint8_t* row = fspin + gy * FL;
@@ -1024,7 +1060,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__
     uint64_t x0, y0;
     int w, h;
     tile_geom(lat, t, TH, x0, y0, w, h);
-    const uint32_t tx = t % lat.ntx, ty = t / lat.ntx;
+    uint32_t tx, ty;
+    tile_xy(lat, t, tx, ty);
     const uint32_t* bits = b.ebits + (uint64_t)t * R::kBitWords;
     const uint16_t* edge = b.edge + (uint64_t)t * R::kEdge;
     if (pos < TH) {
