@@ -431,6 +431,25 @@ __device__ __forceinline__ uint32_t zero_bytes4(uint32_t x) {
   return ((t >> 7) * 0x01020408u) >> 24;
 }
 
+// Bit k = (w[k] < thr), k = 0..3: the carry-out of each subtraction w[k] -
+// thr (PTX sub.cc; set when no borrow occurs, i.e. w[k] >= thr) is shifted
+// into d by an add with carry-in (addc: d = 2d + carry), highest k first,
+// and the four bits are inverted.
+__device__ __forceinline__ uint32_t lt_mask4(const uint32_t (&w)[4], uint32_t thr) {
+  uint32_t d = 0, t;
+  asm("sub.cc.u32 %1, %2, %6;\n\t"
+      "addc.u32 %0, %0, %0;\n\t"
+      "sub.cc.u32 %1, %3, %6;\n\t"
+      "addc.u32 %0, %0, %0;\n\t"
+      "sub.cc.u32 %1, %4, %6;\n\t"
+      "addc.u32 %0, %0, %0;\n\t"
+      "sub.cc.u32 %1, %5, %6;\n\t"
+      "addc.u32 %0, %0, %0;"
+      : "+r"(d), "=&r"(t)
+      : "r"(w[3]), "r"(w[2]), "r"(w[1]), "r"(w[0]), "r"(thr));
+  return ~d & 0xFu;
+}
+
 __device__ __forceinline__ uint32_t byte_mask(uint32_t nib) {
   // 4-bit site mask -> 0xFF per selected byte
   return ((nib & 1u) ? 0x000000FFu : 0u) | ((nib & 2u) ? 0x0000FF00u : 0u) |
@@ -742,12 +761,8 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
               ud |= (wd[k] < td[k] ? 1u : 0u) << k;
             }
           } else {
-            const uint32_t thr = b.thr;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              ur |= (wr[k] < thr ? 1u : 0u) << k;
-              ud |= (wd[k] < thr ? 1u : 0u) << k;
-            }
+            ur = lt_mask4(wr, b.thr);
+            ud = lt_mask4(wd, b.thr);
           }
           br = eqr & ur;
           bd = eqd & ud;
