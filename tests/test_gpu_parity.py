@@ -347,6 +347,34 @@ def test_sweep_host_overlapped_upload_matches_oracle(L, tile_h):
         s.sync()
 
 
+def test_sweep_host_sixteen_band_plan_equals_the_unbanded_sweep():
+    """L = 32768 with 16-row tiles has 2048 tile rows: the doubling band
+    plan reaches its 16-band limit and the last band takes the rest.  The
+    banded host-driven sweep must give exactly the configuration and the
+    observables of sw_set_spins + sw_sweep (oracle-checked on its own)."""
+    import torch
+    L, q = 32768, 2
+    T = sw.tc(q)
+    rng = np.random.default_rng(77)
+    s0 = torch.from_numpy(rng.integers(0, q, size=L * L, dtype=np.uint8)).pin_memory()
+    with sw.Sim(L, q, T, 9, tile_h=16) as a:
+        E1, n1, c1 = a.sweep_host(s0.numpy(), 2)
+        d1 = torch.empty(L * L, dtype=torch.uint8, device="cuda")
+        a.spins(out=d1)
+        a.sync()
+    with sw.Sim(L, q, T, 9, tile_h=16) as b:
+        b.set_spins(s0.numpy())
+        b.sweep(2)
+        E2, n2, c2 = b.measure()
+        d2 = torch.empty(L * L, dtype=torch.uint8, device="cuda")
+        b.spins(out=d2)
+        b.sync()
+    assert (E1, c1) == (E2, c2) and np.array_equal(n1, n2)
+    assert torch.equal(d1, d2)
+    del d1, d2
+    torch.cuda.empty_cache()
+
+
 def test_sweep_host_rejects_an_invalid_configuration():
     L, q = 96, 2
     with sw.Sim(L, q, sw.tc(q), 3) as s:
