@@ -1,0 +1,901 @@
+// sw_label.cuh -- k_label_rows, the tile labeller of the Potts sweep with
+// one lane per half tile row.
+//
+// It computes what k_label_tile computes (Sec. 2 steps (1)-(3), tile-local
+// part, plus the measurement of Sec. 4) and writes the same records -- the
+// 16-bit site codes, the four edge lines, the cross-edge bond bits, the
+// open-root list and the initial global labels -- so that k_merge, k_resolve
+// and k_recolor run unchanged after it.  What differs is the work mapping:
+//
+//   * a lane owns 64 consecutive sites of one tile row (two 32-bit words),
+//     so a warp covers 16 rows of a 128-wide tile and a CTA of TH/16 warps
+//     the whole 128 x TH tile;
+//   * spins are packed into bit planes (q <= 4), so the equal-neighbour
+//     tests, the E_sat / n[s] counts and the horizontal runs are word
+//     operations on 32 sites at a time; the row below comes from the lane
+//     that owns it (one shuffle per word);
+//   * run starts are a bit mask, and a site's run start is the highest set
+//     bit at or below it: only run starts are union-find nodes, and no
+//     per-site parent is ever written;
+//   * the union-find entries are 16 bits (tile-local index j = ly*128 + lx),
+//     so a 128 x 64 tile needs 16 KB of shared memory; linking a root is a
+//     compare-and-swap of the 32-bit word that holds its entry.
+//
+// Phases of a tile (a barrier after each):
+//   A  bonds (Philox, one call per two sites), observables of the
+//      configuration read, cross-edge bond bits, run-start masks;
+//   B  vertical unions: each lane links its row to the row below over its
+//      64 columns, one union per vertical bond that does not repeat its
+//      left neighbour's pair of runs;
+//   C  clusters that touch the tile edge are flagged open at their root;
+//   D  run starts are compressed to their root; a closed cluster draws its
+//      new state at its root (Sec. 2 step (3)), an open root takes a slot in
+//      the tile's open list and a global label;
+//   F  per-site codes (16 sites' worth of lanes per row, coalesced 16-byte
+//      stores) and the edge lines.
+//
+// Entry encoding in P: a plain index (< 0x4000) is a parent (a root names
+// itself); phase C adds 0x8000 to open roots; phase D replaces every root's
+// entry by its code, 0x8000 | payload (closed: the new state, or the root
+// index in the labelling-only form) or 0x4000 | slot (open), so that phase
+// F walks from a run start to the first entry with a marker.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sw_kernels.cuh"
+
+namespace swgb {
+
+constexpr uint32_t kIdx16 = 0x3FFFu;    // index bits of a 16-bit entry
+constexpr uint32_t kMarkA = 0x8000u;    // open flag of a root; closed code marker
+constexpr uint32_t kMarkB = 0x4000u;    // open code marker
+constexpr uint32_t kMarks = kMarkA | kMarkB;
+
+// CTA shape: a lane owns kW words (32 sites each) of a row, kLpr lanes a
+// row, kRpw rows a warp.
+template <int TH>
+struct RowCta {
+  static constexpr int kW = 2;
+  static constexpr int kLpr = 4 / kW;
+  static constexpr int kRpw = 32 / kLpr;
+  static constexpr int kWarps = TH / kRpw;
+  static constexpr int kThreads = 32 * kWarps;
+  static constexpr int kMinBlocks = 1024 / kThreads;  // 64 registers a thread
+  static_assert(TH % kRpw == 0, "tile height");
+  // a warp's work queue in the staging buffer: 512 entries (32 lanes x 16)
+  static constexpr int kQCap = (TH + 1) * 128 / 4 / kWarps;
+  static_assert(kQCap >= 512, "work queue");
+};
+
+// Shared memory of k_label_rows.
+template <int TH>
+struct RowSmem {
+  static constexpr int kP = 0;                                          // u16 [TH*128]
+  static constexpr int kSp = align16(kP + 2 * kTW * TH);                 // u8 [(TH+1)*128], swizzled
+  static constexpr int kHal = kSp + (TH + 1) * kTW;                      // u8 [TH+1][4] halo column
+  static constexpr int kRS = align16(kHal + 4 * (TH + 1));               // u32 [TH][4] run starts
+  static constexpr int kRC = kRS + 16 * TH;                              // u8 [TH][4] run start of bit 0
+  static constexpr int kNR = align16(kRC + 4 * TH);                      // u32 [TH][4] linked (non-root) starts
+  static constexpr int kCb = align16(kNR + 16 * TH);                     // u32 cross bits
+  static constexpr int kCnt = align16(kCb + 4 * TileRec<TH>::kBitWords);  // u32 [4]
+  static constexpr int kObs = kCnt + 16;                                 // u32 [8], or [257] for q > 4
+  static constexpr int kBytesSmallQ = align16(kObs + 4 * 8);
+  static constexpr int kBytes = align16(kObs + 4 * 257);
+};
+
+// ---------------------------------------------------------------- 16-bit union-find
+// Root of x after the unions (entries may carry the open flag).
+__device__ __forceinline__ uint32_t root16(const uint16_t* P, uint32_t x, uint32_t& bad) {
+  const volatile uint16_t* vp = P;
+  for (uint32_t it = 0; it < kLocalCap; ++it) {
+    const uint32_t p = vp[x] & kIdx16;
+    if (p == x) return x;
+    x = p;
+  }
+  bad = 1;
+  return x;
+}
+
+// Run start of bit b of a word whose starts are m, columns from cw; c is the
+// run start of bit 0 (a run that begins in an earlier word).
+__device__ __forceinline__ uint32_t run_start(uint32_t m, int b, uint32_t cw, uint32_t c) {
+  const uint32_t mm = m & (0xFFFFFFFFu >> (31 - b));
+  return mm ? cw + 31u - (uint32_t)__clz(mm) : c;
+}
+
+// Run start of column c0 + x of a lane's 64 columns whose starts are m; c
+// is the run start of the lane's first column (a run from an earlier part).
+__device__ __forceinline__ uint32_t run_start64(uint64_t m, uint32_t x, uint32_t c0, uint32_t c) {
+  const uint64_t mm = m & (0xFFFFFFFFFFFFFFFFull >> (63u - x));
+  return mm ? c0 + 63u - (uint32_t)__clzll(mm) : c;
+}
+
+// Warp work queue: each lane appends up to 16 of its remaining items (the
+// set bits of rem, lowest first, as f(bit)) to Q; returns how many the warp
+// queued.  Entries are ordered by lane, each lane's contiguous.
+template <typename Fn>
+__device__ __forceinline__ uint32_t enqueue16(uint64_t& rem, uint32_t* Q, int lane, Fn f) {
+  const uint32_t cnt = min((uint32_t)__popcll(rem), 16u);
+  uint32_t inc = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  const uint32_t nq = __shfl_sync(0xFFFFFFFFu, inc, 31);
+  uint32_t pos = inc - cnt;
+  for (uint32_t k = 0; k < cnt; ++k) {
+    const uint32_t x = (uint32_t)(__ffsll(rem) - 1);
+    rem &= rem - 1ull;
+    Q[pos++] = f(x);
+  }
+  __syncwarp();
+  return nq;
+}
+
+// Bit k of the result = bit `pl` of byte k of w (k = 0..3).
+__device__ __forceinline__ uint32_t plane4(uint32_t w, int pl) {
+  return ((((w >> pl) & 0x01010101u) * 0x01020408u) >> 24) & 0xFu;
+}
+
+// Staged spin rows are 128 bytes apart with their eight 16-byte chunks
+// permuted by the row (chunk k of row y at position k ^ (y & 7)), so that
+// the lanes of a warp, each reading its own row, hit distinct banks.  Byte
+// offset of (row y, column col < 128):
+__device__ __forceinline__ uint32_t swz(int y, int col) {
+  return (uint32_t)(y * kTW + ((((col >> 4) ^ y) & 7) << 4) + (col & 15));
+}
+
+// The 32 sites at columns col .. col+31 of staged row y (col a multiple of
+// 16) as one word of bit plane 0 and one of bit plane 1.
+__device__ __forceinline__ void pack32(const uint8_t* sp, int y, int col, bool two, uint32_t& p0, uint32_t& p1) {
+  const uint4 u = *reinterpret_cast<const uint4*>(sp + swz(y, col));
+  const uint4 v = *reinterpret_cast<const uint4*>(sp + swz(y, col + 16));
+  const uint32_t w[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+  uint32_t a = 0, c = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a |= plane4(w[k], 0) << (4 * k);
+  if (two) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) c |= plane4(w[k], 1) << (4 * k);
+  }
+  p0 = a;
+  p1 = c;
+}
+
+// Even / odd bits of a 32-bit word, compacted into 16 bits (bond bytes:
+// bit 2k = right bond of site k, bit 2k+1 = down bond).
+__device__ __forceinline__ uint32_t even_bits(uint32_t x) {
+  x &= 0x55555555u;
+  x = (x | (x >> 1)) & 0x33333333u;
+  x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+  x = (x | (x >> 4)) & 0x00FF00FFu;
+  x = (x | (x >> 8)) & 0x0000FFFFu;
+  return x;
+}
+
+// Stages a tile's spin rows 0..h (row h is the halo row) into buf (the
+// swizzled layout of swz) and each row's halo byte (column w) at column w of
+// the row when the tile is narrower than 128, else into hal[4*y];
+// asynchronous (cp.async) when rows are 4-byte aligned, with 16-byte copies
+// when L % 16 == 0.
+template <int TH, int kThreads, typename Src>
+__device__ __forceinline__ void stage_rows(const Src& src, uint32_t gg, uint8_t* buf, uint8_t* hal, bool async) {
+  constexpr int kWarps = kThreads / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t fr = src.rep(gg);
+  const Lattice& fl = src.lattice(fr);
+  const uint8_t* fspin = src.bufs(fr).spin;
+  const uint64_t FL = fl.L;
+  uint64_t fx0, fy0;
+  int fw, fh;
+  tile_geom(fl, gg - src.tile0(fr), TH, fx0, fy0, fw, fh);
+  const uint64_t hx = (fx0 + fw == FL) ? 0 : fx0 + fw;
+  const uint64_t hy = (fy0 + fh == FL) ? 0 : fy0 + fh;
+  if (async && (FL & 15u) == 0 && (reinterpret_cast<uintptr_t>(fspin) & 15u) == 0) {
+    const int c16 = (lane & 7) * 16;
+    for (int ly = warp * 4 + (lane >> 3); ly <= fh; ly += 4 * kWarps) {
+      const uint64_t gy = (ly < fh) ? (fy0 + ly) : hy;
+      if (c16 < fw) cp_async16(buf + swz(ly, c16), fspin + gy * FL + fx0 + c16);
+    }
+    for (int ly = tid; ly <= fh; ly += kThreads) {
+      const uint64_t gy = (ly < fh) ? (fy0 + ly) : hy;
+      cp_async4(fw < kTW ? buf + swz(ly, fw) : hal + 4 * ly, fspin + gy * FL + hx);
+    }
+    return;
+  }
+  const int lx0 = 4 * lane;  // 32 lanes x 4 bytes: the 128 columns
+  for (int ly = warp; ly <= fh; ly += kWarps) {
+    const uint64_t gy = (ly < fh) ? (fy0 + ly) : hy;
+    const uint8_t* row = fspin + gy * FL;
+    if (async) {
+      if (lx0 < fw) cp_async4(buf + swz(ly, lx0), row + fx0 + lx0);
+      if (lane == 31) cp_async4(fw < kTW ? buf + swz(ly, fw) : hal + 4 * ly, row + hx);
+    } else {
+      uint32_t v = 0;
+      if (lx0 < fw) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (lx0 + k < fw) v |= (uint32_t)row[fx0 + lx0 + k] << (8 * k);
+      }
+      *reinterpret_cast<uint32_t*>(buf + swz(ly, lx0)) = v;
+      __syncwarp();
+      if (lane == 0) {
+        if (fw < kTW) buf[swz(ly, fw)] = row[hx];
+        else hal[4 * ly] = row[hx];
+      }
+    }
+  }
+}
+
+// ================================================================== k_label_rows
+// Persistent: CTA c labels tiles c, c + gridDim.x, ...; the next tile's spins
+// are copied into the staging buffer as soon as the bonds of the current
+// one are drawn.
+//
+// kGiven: bonds are read from b.bonds instead of drawn (labelling-only entry).
+// kRoots: closed clusters keep their local root in the code (no new state).
+template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src>
+__global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
+    k_label_rows(const __grid_constant__ Src src) {
+  using C = RowCta<TH>;
+  using S = RowSmem<TH>;
+  using R = TileRec<TH>;
+  constexpr int kW = C::kW, kLpr = C::kLpr, kRpw = C::kRpw, kThreads = C::kThreads, kQCap = C::kQCap;
+  constexpr unsigned kFull = 0xFFFFFFFFu;
+
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint16_t* P = reinterpret_cast<uint16_t*>(smem + S::kP);
+  uint8_t* sp = smem + S::kSp;
+  uint8_t* hal = smem + S::kHal;
+  uint32_t* RS = reinterpret_cast<uint32_t*>(smem + S::kRS);
+  uint8_t* RC = smem + S::kRC;
+  uint32_t* NR = reinterpret_cast<uint32_t*>(smem + S::kNR);
+  uint32_t* cbits = reinterpret_cast<uint32_t*>(smem + S::kCb);
+  uint32_t* wcnt = reinterpret_cast<uint32_t*>(smem + S::kCnt);
+  uint32_t* sobs = reinterpret_cast<uint32_t*>(smem + S::kObs);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int part = lane % kLpr;
+  const int ly = warp * kRpw + lane / kLpr;  // this lane's row
+  const int c0 = part * 32 * kW;             // its first column
+  const uint32_t total = src.ntiles();
+  uint32_t bad = 0, spin_max = 0;
+  const bool big_q = !kGiven && src.bufs(0).q > 4 && !Src::kMulti;  // shared state histogram
+
+  for (int k = tid; k < (Src::kMulti ? 257 : (big_q ? 257 : 8)); k += kThreads) sobs[k] = 0;
+  for (int k = tid; k < R::kBitWords; k += kThreads) cbits[k] = 0;
+  uint32_t e_loc = 0, nsites = 0;
+  uint32_t ncnt[3] = {0, 0, 0};
+
+  // observables accumulated so far go to the lattice's accumulator (E_sat,
+  // bit-plane counts c1 = n1 + n3, c2 = n2 + n3, c3 = n3 for q <= 4, n[s]
+  // in shared memory otherwise; n[0] from the site count).  All threads.
+  auto flush = [&](const Bufs& fb, uint32_t fq) {
+    const bool fregs = fq <= 4;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e_loc += __shfl_xor_sync(kFull, e_loc, o);
+    if (lane == 0) atomicAdd(&sobs[0], e_loc);
+    if (fregs) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ncnt[k] += __shfl_xor_sync(kFull, ncnt[k], o);
+      if (lane == 0) {
+        atomicAdd(&sobs[2], ncnt[0] - ncnt[2]);
+        if (fq > 2) atomicAdd(&sobs[3], ncnt[1] - ncnt[2]);
+        if (fq > 3) atomicAdd(&sobs[4], ncnt[2]);
+      }
+    }
+    __syncthreads();
+    if (fregs && tid == 0) {
+      uint32_t rest = nsites;
+      for (uint32_t st = 1; st < fq; ++st) rest -= sobs[1 + st];
+      sobs[1] = rest;
+    }
+    __syncthreads();
+    for (uint32_t k = tid; k <= fq; k += kThreads)
+      if (sobs[k]) atomicAdd(&fb.acc[k], (unsigned long long)sobs[k]);
+    __syncthreads();
+    for (uint32_t k = tid; k <= fq; k += kThreads) sobs[k] = 0;
+    e_loc = 0;
+    nsites = 0;
+    ncnt[0] = ncnt[1] = ncnt[2] = 0;
+  };
+
+  bool pre = false;
+  if (!kGiven && blockIdx.x < total && src.lattice(src.rep(blockIdx.x)).vec4) {
+    stage_rows<TH, kThreads>(src, blockIdx.x, sp, hal, true);
+    cp_async_commit();
+    pre = true;
+  }
+
+  for (uint32_t g = blockIdx.x; g < total; g += gridDim.x) {
+    const uint32_t rep = src.rep(g);
+    const Bufs& b = src.bufs(rep);
+    const Lattice& lat = src.lattice(rep);
+    const uint32_t t = g - src.tile0(rep);
+    const uint64_t L = lat.L;
+    const uint32_t q_states = b.q;
+    const bool measure = !kGiven && b.measure;
+    const uint32_t sweep = kGiven ? 0u : (uint32_t)b.ctl[0];
+    LabelT* T = reinterpret_cast<LabelT*>(b.T);
+    uint64_t x0, y0;
+    int w, h;
+    tile_geom(lat, t, TH, x0, y0, w, h);
+    if (!kGiven) {
+      if (pre) cp_async_wait();
+      else stage_rows<TH, kThreads>(src, g, sp, hal, false);
+    }
+    if (tid == 0) nsites += (uint32_t)(w * h);
+    __syncthreads();  // staged spins visible; the previous tile is done with every shared array
+
+    // ================================================= A: bonds, observables, runs
+    uint32_t vm[kW], H[kW], V[kW], Sm[kW], Cw[kW];
+#pragma unroll
+    for (int wi = 0; wi < kW; ++wi) {
+      const int nv = w - (c0 + 32 * wi);
+      vm[wi] = (ly < h) ? (nv >= 32 ? 0xFFFFFFFFu : (nv > 0 ? (1u << nv) - 1u : 0u)) : 0u;
+      H[wi] = V[wi] = 0;
+    }
+    if constexpr (kGiven) {
+      if (ly < h) {
+        const uint8_t* brow = b.bonds + (y0 + ly) * lat.bp;
+#pragma unroll
+        for (int wi = 0; wi < kW; ++wi) {
+          if (vm[wi]) {
+            const uint64_t byte0 = (x0 + c0 + 32 * wi) >> 2;
+            uint32_t lo = 0, hi = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const uint32_t v = (byte0 + k < lat.bp) ? (uint32_t)brow[byte0 + k] : 0u;
+              if (k < 4) lo |= v << (8 * k);
+              else hi |= v << (8 * (k - 4));
+            }
+            H[wi] = (even_bits(lo) | (even_bits(hi) << 16)) & vm[wi];
+            V[wi] = (even_bits(lo >> 1) | (even_bits(hi >> 1) << 16)) & vm[wi];
+          }
+        }
+      }
+    } else {
+      const uint32_t np = q_states <= 2 ? 1u : (q_states <= 4 ? 2u : 0u);  // bit planes
+      uint32_t eqr[kW], eqd[kW];
+      if (np) {
+        const bool two = np == 2;
+        uint32_t a0[kW], a1[kW], d0[kW], d1[kW];
+#pragma unroll
+        for (int wi = 0; wi < kW; ++wi) a0[wi] = a1[wi] = 0;
+        uint32_t nb = 0;  // the byte right of this lane's range (last part: the halo column)
+        if (ly <= h) {
+#pragma unroll
+          for (int wi = 0; wi < kW; ++wi) pack32(sp, ly, c0 + 32 * wi, two, a0[wi], a1[wi]);
+          if (part == kLpr - 1) nb = hal[4 * ly];  // column 128 (a narrower tile masks it)
+          if constexpr (Src::kCheck) {
+            if (ly < h) {
+#pragma unroll
+              for (int k = 0; k < 8 * kW; ++k) {
+                const int cc = c0 + 4 * k;
+                const int nv = w - cc;
+                const uint32_t m4 = nv >= 4 ? 0xFu : (nv > 0 ? (1u << nv) - 1u : 0u);
+                spin_max = __vmaxu4(spin_max, *reinterpret_cast<const uint32_t*>(sp + swz(ly, cc)) & byte_mask(m4));
+              }
+            }
+          }
+        }
+        // right neighbours: bit 0 of the next part of the row, or the halo byte
+        const uint32_t n0 = __shfl_down_sync(kFull, a0[0], 1), n1 = __shfl_down_sync(kFull, a1[0], 1);
+        const uint32_t nr0 = part == kLpr - 1 ? (nb & 1u) : (n0 & 1u);
+        const uint32_t nr1 = part == kLpr - 1 ? ((nb >> 1) & 1u) : (n1 & 1u);
+        // the row below: from the lane that owns it, or staged (last row of the warp)
+#pragma unroll
+        for (int wi = 0; wi < kW; ++wi) {
+          d0[wi] = __shfl_down_sync(kFull, a0[wi], kLpr);
+          d1[wi] = __shfl_down_sync(kFull, a1[wi], kLpr);
+        }
+        if (lane / kLpr == kRpw - 1 && ly < h) {
+#pragma unroll
+          for (int wi = 0; wi < kW; ++wi) pack32(sp, ly + 1, c0 + 32 * wi, two, d0[wi], d1[wi]);
+        }
+#pragma unroll
+        for (int wi = 0; wi < kW; ++wi) {
+          const uint32_t x0n = wi + 1 < kW ? (a0[wi + 1] & 1u) : nr0;
+          const uint32_t x1n = wi + 1 < kW ? (a1[wi + 1] & 1u) : nr1;
+          const uint32_t r0 = (a0[wi] >> 1) | (x0n << 31), r1 = (a1[wi] >> 1) | (x1n << 31);
+          eqr[wi] = ~((a0[wi] ^ r0) | (a1[wi] ^ r1)) & vm[wi];
+          eqd[wi] = ~((a0[wi] ^ d0[wi]) | (a1[wi] ^ d1[wi])) & vm[wi];
+          if (measure) {
+            e_loc += __popc(eqr[wi]) + __popc(eqd[wi]);
+            ncnt[0] += __popc(a0[wi] & vm[wi]);
+            if (two) {
+              ncnt[1] += __popc(a1[wi] & vm[wi]);
+              ncnt[2] += __popc(a0[wi] & a1[wi] & vm[wi]);
+            }
+          }
+        }
+      } else {
+        // q > 4: byte-wise comparisons, state counts in a shared histogram
+#pragma unroll
+        for (int wi = 0; wi < kW; ++wi) {
+          eqr[wi] = eqd[wi] = 0;
+          if (ly < h) {
+#pragma unroll
+            for (int gq = 0; gq < 8; ++gq) {
+              const uint32_t sh = 4 * gq;
+              const int cc = c0 + 32 * wi + 4 * gq;
+              const uint32_t m4 = (vm[wi] >> sh) & 0xFu;
+              const uint32_t s = *reinterpret_cast<const uint32_t*>(sp + swz(ly, cc));
+              const uint32_t sn = cc + 4 < kTW ? *reinterpret_cast<const uint32_t*>(sp + swz(ly, cc + 4))
+                                                : *reinterpret_cast<const uint32_t*>(hal + 4 * ly);
+              const uint32_t sd = *reinterpret_cast<const uint32_t*>(sp + swz(ly + 1, cc));
+              if constexpr (Src::kCheck) spin_max = __vmaxu4(spin_max, s & byte_mask(m4));
+              const uint32_t er = zero_bytes4(s ^ __funnelshift_r(s, sn, 8)) & m4;
+              const uint32_t ed = zero_bytes4(s ^ sd) & m4;
+              eqr[wi] |= er << sh;
+              eqd[wi] |= ed << sh;
+              if (measure) {
+                e_loc += __popc(er) + __popc(ed);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                  if (m4 & (1u << k)) atomicAdd(&sobs[1 + ((s >> (8 * k)) & 0xFFu)], 1u);
+              }
+            }
+          }
+        }
+      }
+      // bond draws: one Philox call per two sites (right and down words)
+      const uint64_t rowg = (y0 + ly) * L + x0 + c0;
+#pragma unroll
+      for (int wi = 0; wi < kW; ++wi) {
+#pragma unroll 2
+        for (int gq = 0; gq < 8; ++gq) {
+          const uint32_t sh = 4 * gq;
+          const uint32_t er = (eqr[wi] >> sh) & 0xFu, ed = (eqd[wi] >> sh) & 0xFu;
+          uint32_t br = 0, bd = 0;
+          if (er | ed) {
+            const uint64_t i0 = rowg + 32 * wi + sh;
+            const uint64_t pa = i0 >> 1;
+            const Words4 A = stream4_rk(b.rk, pa, sweep, kDomBond);
+            const Words4 B = stream4_rk(b.rk, pa + 1, sweep, kDomBond);
+            uint32_t wr[4], wd[4];
+            if ((i0 & 1u) == 0u) {
+              wr[0] = A.x; wd[0] = A.y; wr[1] = A.z; wd[1] = A.w;
+              wr[2] = B.x; wd[2] = B.y; wr[3] = B.z; wd[3] = B.w;
+            } else {
+              const Words4 Cc = stream4_rk(b.rk, pa + 2, sweep, kDomBond);
+              wr[0] = A.z; wd[0] = A.w; wr[1] = B.x; wd[1] = B.y;
+              wr[2] = B.z; wd[2] = B.w; wr[3] = Cc.x; wd[3] = Cc.y;
+            }
+            br = er & lt_mask4(wr, b.thr);
+            bd = ed & lt_mask4(wd, b.thr);
+            H[wi] |= br << sh;
+            V[wi] |= bd << sh;
+          }
+          if (b.bonds && ((vm[wi] >> sh) & 0xFu)) {
+            uint32_t byte = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              byte |= (((br >> k) & 1u) << (2 * k)) | (((bd >> k) & 1u) << (2 * k + 1));
+            b.bonds[(y0 + ly) * lat.bp + ((x0 + c0 + 32 * wi + sh) >> 2)] = (uint8_t)byte;
+          }
+        }
+      }
+    }
+    // bonds that leave the tile: right edge (column w-1) and bottom edge
+    if (ly < h) {
+      const int e = w - 1 - c0;
+#pragma unroll
+      for (int wi = 0; wi < kW; ++wi) {
+        if (e >= 32 * wi && e < 32 * wi + 32) {
+          const uint32_t bit = 1u << (e - 32 * wi);
+          if (H[wi] & bit) atomicOr(&cbits[ly >> 5], 1u << (ly & 31));
+          H[wi] &= ~bit;
+        }
+      }
+      if (ly == h - 1) {
+#pragma unroll
+        for (int wi = 0; wi < kW; ++wi) {
+          if (c0 + 32 * wi < w) cbits[R::kRightWords + (c0 >> 5) + wi] = V[wi];
+          V[wi] = 0;
+        }
+      }
+    }
+    // horizontal runs: a site without a bond to its left starts a run
+    {
+      uint32_t hp = __shfl_up_sync(kFull, H[kW - 1] >> 31, 1);
+      if (part == 0) hp = 0;
+#pragma unroll
+      for (int wi = 0; wi < kW; ++wi) Sm[wi] = ~((H[wi] << 1) | (wi ? H[wi - 1] >> 31 : hp)) & vm[wi];
+      int lst = -1;
+#pragma unroll
+      for (int wi = 0; wi < kW; ++wi)
+        if (Sm[wi]) lst = c0 + 32 * wi + 31 - __clz(Sm[wi]);
+      int cin = __shfl_up_sync(kFull, lst, 1);
+      if (part == 0 || cin < 0) cin = 0;
+      Cw[0] = (uint32_t)cin;
+#pragma unroll
+      for (int wi = 1; wi < kW; ++wi)
+        Cw[wi] = Sm[wi - 1] ? (uint32_t)(c0 + 32 * (wi - 1) + 31 - __clz(Sm[wi - 1])) : Cw[wi - 1];
+#pragma unroll
+      for (int wi = 0; wi < kW; ++wi) {
+        RS[ly * 4 + (c0 >> 5) + wi] = Sm[wi];
+        RC[ly * 4 + (c0 >> 5) + wi] = (uint8_t)Cw[wi];
+        NR[ly * 4 + (c0 >> 5) + wi] = 0u;
+      }
+    }
+    // every entry of the row names itself (only run starts are ever used);
+    // the eight 16-byte chunks in a lane-rotated order (no bank conflicts)
+    if (ly < h) {
+      const uint32_t j0 = (uint32_t)(ly * kTW + c0);
+      uint4* dst = reinterpret_cast<uint4*>(P + j0);
+#pragma unroll
+      for (int k = 0; k < 4 * kW; ++k) {
+        const uint32_t ch = (uint32_t)(k + lane) & (4 * kW - 1);
+        const uint32_t v = (j0 + 8 * ch) | ((j0 + 8 * ch + 1) << 16);
+        dst[ch] = make_uint4(v, v + 0x00020002u, v + 0x00040004u, v + 0x00060006u);
+      }
+    }
+    __syncthreads();  // (1) runs, cross bits and entries of every row
+
+    if (tid < R::kBitWords) b.ebits[(uint64_t)t * R::kBitWords + tid] = cbits[tid];
+    // from here to phase F the staging buffer holds the warps' work queues
+    uint32_t* Q = reinterpret_cast<uint32_t*>(sp) + warp * kQCap;
+
+    // ================================================= B: vertical unions
+    // Each lane looks at the vertical bonds from its row y to the row below
+    // over its 64 columns.  Only the first bond of each stretch along which
+    // both rows continue horizontally counts (the others join the same two
+    // runs).  The first such bond of each run of row y+1 (FM) gives that
+    // run a parent: in a top-down pass over the tile's rows (one thread per
+    // column, a barrier per row), its start is pointed at the root of the
+    // row-y run it meets, which is one lookup away because row y is already
+    // done.  This forest needs no atomics, its trees have depth one, and its
+    // roots are the smallest index of their tree.  The remaining bonds (a
+    // run of row y+1 meeting a second run above) join two trees: they are
+    // queued and taken by the warp's lanes in lockstep, one step of their
+    // current task per iteration (both endpoints move up to two levels,
+    // path splitting on the way; a pair of roots is linked by a
+    // compare-and-swap of the word holding the larger one's entry, the
+    // larger under the smaller).  Every start given a parent is marked in
+    // NR; a finished task points both run starts at the root.
+    {
+      uint32_t* FM = reinterpret_cast<uint32_t*>(sp);  // [TH][4] first bonds (staging buffer)
+      const bool pv = ly + 1 < h;  // V is zero otherwise (phase A)
+      const uint4 sq = pv ? *reinterpret_cast<const uint4*>(RS + (ly + 1) * 4) : make_uint4(0u, 0u, 0u, 0u);
+      // the row below over this lane's columns: run starts, the run start of
+      // the first column, whether the column after the last continues a run
+      const uint64_t S1 = part == 0 ? ((uint64_t)sq.x | ((uint64_t)sq.y << 32))
+                                    : ((uint64_t)sq.z | ((uint64_t)sq.w << 32));
+      const uint32_t c1 = part == 0 ? 0u : (sq.y ? 63u - (uint32_t)__clz(sq.y) : 31u - (uint32_t)__clz(sq.x));
+      const uint64_t nb1 = part == 0 ? (uint64_t)(sq.z & 1u) : 1ull;
+      const uint64_t h1 = ~((S1 >> 1) | (nb1 << 63));  // row y+1 continues from column x to x+1
+      const uint64_t Sa = (uint64_t)Sm[0] | ((uint64_t)Sm[1] << 32);
+      const uint64_t Ha = (uint64_t)H[0] | ((uint64_t)H[1] << 32);
+      const uint64_t Va = (uint64_t)V[0] | ((uint64_t)V[1] << 32);
+      // carry-lookahead over a lane's 64 columns: the carry into column x of
+      // gen + (gen | prop) is set iff a generating column x' < x reaches x
+      // through propagating columns.  Tasks: bonds not reached by an earlier
+      // bond along columns where both rows continue.
+      const uint64_t g = Ha & h1 & 0x7FFFFFFFFFFFFFFFull;
+      const uint64_t gen = Va & g;
+      const uint64_t tk = Va & ~((gen + (gen | g)) ^ gen ^ (gen | g));
+      // first task of each run of row y+1 (the run that continues into the
+      // second part of the row carries the answer across)
+      const uint64_t gc = tk & h1;
+      const uint64_t cov0 = (gc + h1) ^ gc ^ h1;
+      uint32_t cin = __shfl_up_sync(kFull, (uint32_t)(((cov0 | tk) & h1) >> 63), 1);
+      if (part == 0) cin = 0;
+      const uint64_t first = tk & ~((gc + h1 + cin) ^ gc ^ h1);
+      uint64_t rem = tk & ~first;
+      FM[ly * 4 + (c0 >> 5)] = (uint32_t)first;
+      FM[ly * 4 + (c0 >> 5) + 1] = (uint32_t)(first >> 32);
+      __syncthreads();
+      volatile uint16_t* vp = P;
+      // top-down: row y+1's first-met runs under the roots of row y
+      for (int y = 0; y + 1 < h; ++y) {
+        for (int x = tid; x < w; x += kThreads) {
+          const int wd = y * 4 + (x >> 5);
+          if ((FM[wd] >> (x & 31)) & 1u) {
+            const uint32_t a = run_start(RS[wd], x & 31, (uint32_t)(x & ~31), RC[wd]);
+            const uint32_t c = run_start(RS[wd + 4], x & 31, (uint32_t)(x & ~31), RC[wd + 4]);
+            vp[(y + 1) * kTW + c] = vp[y * kTW + a];
+            atomicOr(&NR[(y + 1) * 4 + (c >> 5)], 1u << (c & 31u));
+          }
+        }
+        __syncthreads();
+      }
+      // the trees joined again by the remaining bonds
+      const uint32_t ja = (uint32_t)(ly * kTW), jc = ja + kTW;
+      volatile uint32_t* vP32 = reinterpret_cast<volatile uint32_t*>(P);
+      for (;;) {
+        const uint32_t nq = enqueue16(rem, Q, lane, [&](uint32_t x) {
+          return (ja + run_start64(Sa, x, (uint32_t)c0, Cw[0])) |
+                 ((jc + run_start64(S1, x, (uint32_t)c0, c1)) << 16);
+        });
+        if (nq == 0) break;  // warp-uniform
+        uint32_t idx = (uint32_t)lane;
+        uint32_t a = 0, c = 0, a0 = 0, c0s = 0;  // idle lanes look at entry 0 (always a valid index)
+        bool act = false;
+        for (uint32_t it = 0;; ++it) {
+          const bool fetch = !act && idx < nq;
+          const uint32_t e = fetch ? Q[idx] : 0u;
+          idx += fetch ? 32u : 0u;
+          a = fetch ? (e & 0xFFFFu) : a;
+          c = fetch ? (e >> 16) : c;
+          a0 = fetch ? a : a0;
+          c0s = fetch ? c : c0s;
+          act = act || fetch;
+          if (!__any_sync(kFull, act)) break;
+          if (it >= kLocalCap) {  // warp-uniform
+            bad = 1;
+            break;
+          }
+          const uint32_t pa = vp[a], pc = vp[c];
+          const uint32_t qa = vp[pa], qc = vp[pc];
+          const bool ra = (pa == a) || (qa == pa), rc = (pc == c) || (qc == pc);
+          if (act && !ra) vp[a] = (uint16_t)qa;
+          if (act && !rc) vp[c] = (uint16_t)qc;
+          a = (pa == a) ? a : ((qa == pa) ? pa : qa);
+          c = (pc == c) ? c : ((qc == pc) ? pc : qc);
+          const bool both = act && ra && rc;
+          const uint32_t hi = a > c ? a : c, lo = a ^ c ^ hi;
+          const uint32_t sh = (hi & 1u) << 4;
+          const uint32_t old = vP32[hi >> 1];
+          bool done = both && a == c;
+          if (both && a != c && ((old >> sh) & 0xFFFFu) == hi) {
+            const uint32_t nw = (old & ~(0xFFFFu << sh)) | (lo << sh);
+            if (atomicCAS(reinterpret_cast<uint32_t*>(P) + (hi >> 1), old, nw) == old) {
+              atomicOr(&NR[hi >> 5], 1u << (hi & 31u));
+              done = true;
+            }
+          }
+          const uint32_t root = lo;
+          if (done && a0 != root) vp[a0] = (uint16_t)root;
+          if (done && c0s != root) vp[c0s] = (uint16_t)root;
+          act = act && !done;
+        }
+        __syncwarp();  // the queue is refilled next round
+      }
+    }
+    __syncthreads();  // (2) every union done
+
+    // ================================================= C: open flags
+    // A cluster that touches the tile edge is open: every edge site flags
+    // its root (row edges: only run starts, the rest of a run shares them).
+    if (tid < R::kBitWords) cbits[tid] = 0;
+    if (tid == 0) wcnt[0] = 0;
+    {
+      const int nedge = 2 * (w + h);
+      for (int e = tid; e < nedge; e += kThreads) {
+        int lx, yy;
+        bool col;
+        if (e < h) { lx = w - 1; yy = e; col = true; }
+        else if (e < 2 * h) { lx = 0; yy = e - h; col = true; }
+        else if (e < 2 * h + w) { lx = e - 2 * h; yy = 0; col = false; }
+        else { lx = e - 2 * h - w; yy = h - 1; col = false; }
+        const uint32_t Sw = RS[yy * 4 + (lx >> 5)];
+        if (!col && !((Sw >> (lx & 31)) & 1u)) continue;
+        const uint32_t st = run_start(Sw, lx & 31, (uint32_t)(lx & ~31), RC[yy * 4 + (lx >> 5)]);
+        const uint32_t r = root16(P, (uint32_t)(yy * kTW) + st, bad);
+        atomicOr(reinterpret_cast<uint32_t*>(P) + (r >> 1), kMarkA << ((r & 1u) << 4));
+      }
+    }
+    // every linked run start is pointed straight at its root, so that a
+    // site's code is at most two lookups away in phase F: the lanes queue
+    // their linked starts and walk them in lockstep, two links per
+    // iteration (path splitting on the way)
+    {
+      volatile uint16_t* vp = P;
+      uint64_t rem = 0;
+      if (ly < h)
+        rem = ((uint64_t)Sm[0] & NR[ly * 4 + (c0 >> 5)]) |
+              (((uint64_t)Sm[1] & NR[ly * 4 + (c0 >> 5) + 1]) << 32);
+      const uint32_t jb = (uint32_t)(ly * kTW + c0);
+      for (;;) {
+        const uint32_t nq = enqueue16(rem, Q, lane, [&](uint32_t x) { return jb + x; });
+        if (nq == 0) break;  // warp-uniform
+        uint32_t idx = (uint32_t)lane, sj = 0, x = 0;  // idle lanes look at entry 0
+        bool act = false;
+        for (uint32_t it = 0;; ++it) {
+          const bool fetch = !act && idx < nq;
+          const uint32_t e = fetch ? Q[idx] : 0u;
+          idx += fetch ? 32u : 0u;
+          sj = fetch ? e : sj;
+          x = fetch ? e : x;
+          act = act || fetch;
+          if (!__any_sync(kFull, act)) break;
+          if (it >= kLocalCap) {  // warp-uniform
+            bad = 1;
+            break;
+          }
+          // two links towards the root (a root names itself, maybe flagged)
+          const uint32_t p1 = vp[x] & kIdx16;
+          const uint32_t p2 = vp[p1] & kIdx16;
+          const uint32_t p3 = vp[p2] & kIdx16;
+          const bool r1 = p2 == p1, r2 = p3 == p2;
+          if (act && !r1 && !r2) vp[p1] = (uint16_t)p3;  // splitting (p1 is not a root)
+          const bool done = act && (r1 || r2);
+          const uint32_t root = r1 ? p1 : p2;
+          if (done) vp[sj] = (uint16_t)root;
+          x = r1 ? p1 : (r2 ? p2 : p3);
+          act = act && !done;
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();  // (3) flags set
+
+    // ================================================= D: roots
+    // The roots among a lane's run starts are the starts no link marked
+    // (NR).  The lanes queue their roots and take them in lockstep: a
+    // closed root draws its cluster's new state (Sec. 2 step (3)), an open
+    // root (flagged in phase C) takes a slot in the tile's open list (in
+    // whatever order: a slot only names the root to later kernels) and a
+    // global label.  Other starts keep pointing at their root: phase F
+    // looks the code up there.
+    {
+      volatile uint16_t* vp = P;
+      uint64_t rem = 0;
+      if (ly < h)
+        rem = ((uint64_t)Sm[0] & ~NR[ly * 4 + (c0 >> 5)]) |
+              (((uint64_t)Sm[1] & ~NR[ly * 4 + (c0 >> 5) + 1]) << 32);
+      const uint32_t jb = (uint32_t)(ly * kTW + c0);
+      for (;;) {
+        const uint32_t nq = enqueue16(rem, Q, lane, [&](uint32_t x) { return jb + x; });
+        if (nq == 0) break;  // warp-uniform
+        for (uint32_t k0 = 0; k0 < nq; k0 += 32) {
+          const uint32_t k = k0 + (uint32_t)lane;
+          const uint32_t r = k < nq ? Q[k] : 0u;
+          const uint32_t e = vp[r];
+          if (k < nq) {
+            if (e & kMarkA) {
+              const uint32_t slot = atomicAdd(&wcnt[0], 1u);
+              b.olist[(uint64_t)t * R::kOpenCap + slot] = (uint16_t)r;
+              const uint64_t gr = global_index(lat, x0, y0, r);
+              T[gr] = (LabelT)gr;
+              vp[r] = (uint16_t)(kMarkB | slot);
+            } else {
+              uint32_t code;
+              if constexpr (kRoots) {
+                code = kMarkA | r;
+              } else {
+                code = kMarkA |
+                       pick_state(stream4_rk(b.rk, global_index(lat, x0, y0, r), sweep, kDomSpin).x, q_states);
+              }
+              vp[r] = (uint16_t)code;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();  // (4) every root coded
+
+    // the next tile's spins into the staging buffer (free again), while
+    // this tile's codes are written
+    pre = false;
+    if (!kGiven) {
+      const uint32_t gn = g + gridDim.x;
+      if (gn < total && src.lattice(src.rep(gn)).vec4) {
+        stage_rows<TH, kThreads>(src, gn, sp, hal, true);
+        cp_async_commit();
+        pre = true;
+      }
+    }
+
+    // ================================================= F: site codes, edge lines
+    {
+      uint16_t* edge = b.edge + (uint64_t)t * R::kEdge;
+      const volatile uint16_t* vp = P;
+      const int cx = 8 * (tid & 15);
+      for (int yy = tid >> 4; yy < h; yy += kThreads / 16) {
+        if (cx < w) {
+          const uint32_t Sw = RS[yy * 4 + (cx >> 5)];
+          const int sh = cx & 31;
+          const uint32_t s8 = (Sw >> sh) & 0xFFu;
+          const uint32_t jr = (uint32_t)(yy * kTW);
+          uint32_t st = (uint32_t)cx;
+          if (!(s8 & 1u)) {
+            const uint32_t m = Sw & ((1u << sh) - 1u);
+            st = m ? (uint32_t)((cx & ~31) + 31 - __clz(m)) : (uint32_t)RC[yy * 4 + (cx >> 5)];
+          }
+          uint32_t cd[8], rt[8];
+          // a run start's root is the first entry with a marker on its path:
+          // two levels are looked up for every site at once (non-starts
+          // repeat their left neighbour), deeper paths are walked afterwards
+          auto look = [&](uint32_t j, uint32_t& x, uint32_t& e) {
+            const uint32_t e1 = vp[j];
+            x = (e1 & kMarks) ? j : e1;
+            e = vp[x];
+          };
+          bool deep;
+          {
+            uint32_t x, e;
+            look(jr + st, x, e);
+            deep = !(e & kMarks);
+            rt[0] = x;
+            cd[0] = e;
+          }
+          // the group's own eight entries in one 16-byte load; a start's
+          // entry is its code (a root) or its root's index
+          const uint4 E = *reinterpret_cast<const uint4*>(P + jr + cx);
+          const uint32_t ew[4] = {E.x, E.y, E.z, E.w};
+#pragma unroll
+          for (int k = 1; k < 8; ++k) {
+            const bool sk = (s8 >> k) & 1u;
+            const uint32_t e1 = (ew[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
+            const bool mk = (e1 & kMarks) != 0u;
+            const uint32_t x = mk ? jr + cx + k : e1;
+            const uint32_t e = (sk && !mk) ? (uint32_t)vp[x] : e1;
+            deep = deep || (sk && !(e & kMarks));
+            rt[k] = sk ? x : rt[k - 1];
+            cd[k] = sk ? e : cd[k - 1];
+          }
+          if (deep) {  // rare: a start more than two links below its root
+            for (int k = 0; k < 8; ++k) {
+              if (k == 0 || ((s8 >> k) & 1u)) {
+                uint32_t x = rt[k], e = cd[k];
+                for (uint32_t it = 0; !(e & kMarks); ++it) {
+                  if (it >= kLocalCap) {
+                    bad = 1;
+                    break;
+                  }
+                  x = e;
+                  e = vp[x];
+                }
+                rt[k] = x;
+                cd[k] = e;
+              } else {
+                rt[k] = rt[k - 1];
+                cd[k] = cd[k - 1];
+              }
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) cd[k] = (cd[k] & kMarkB) ? (cd[k] & kIdx16) : cd[k];
+          const uint64_t gi = (y0 + yy) * L + x0 + cx;
+          if ((L & 7u) == 0 && cx + 8 <= w) {
+            *reinterpret_cast<uint4*>(b.code + gi) = make_uint4(cd[0] | (cd[1] << 16), cd[2] | (cd[3] << 16),
+                                                                cd[4] | (cd[5] << 16), cd[6] | (cd[7] << 16));
+          } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (cx + k < w) b.code[gi + k] = (uint16_t)cd[k];
+          }
+          if (yy == 0 || yy == h - 1) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              if (cx + k < w) {
+                if (yy == h - 1) edge[2 * TH + cx + k] = (uint16_t)rt[k];
+                if (yy == 0) edge[2 * TH + kTW + cx + k] = (uint16_t)rt[k];
+              }
+            }
+          }
+          if (cx == 0) edge[TH + yy] = (uint16_t)rt[0];
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (cx + k == w - 1) edge[yy] = (uint16_t)rt[k];
+        }
+      }
+      if (tid == 0) b.ocnt[t] = wcnt[0];
+    }
+    // a replica's observables go out when the CTA's next tile belongs to
+    // another replica (or there is none)
+    if (Src::kMulti && measure) {
+      const uint32_t gn = g + gridDim.x;
+      if (gn >= total || src.rep(gn) != rep) flush(b, q_states);
+    }
+  }
+
+  if (!Src::kMulti && !kGiven && total > 0 && blockIdx.x < total) {
+    const Bufs& b0 = src.bufs(0);
+    if (b0.measure) flush(b0, b0.q);
+  }
+  if (bad) atomicOr(src.bufs(0).err, kErrLocal);
+  if constexpr (Src::kCheck) {
+    const uint32_t m2 = __vmaxu4(spin_max, spin_max >> 16);
+    if ((__vmaxu4(m2, m2 >> 8) & 0xFFu) >= src.bufs(0).q) atomicOr(src.bufs(0).err, kErrSpin);
+  }
+}
+
+}  // namespace swgb

@@ -5,45 +5,104 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "sw_kernels.cuh"
+#include "sw_label.cuh"
 
 namespace swgb {
 
-// Sets the kernel's shared-memory attributes and returns how many tile CTAs
-// fit on the GPU at once (done once per instantiation; call it before any
-// stream capture).
-template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY = false>
-cudaError_t configure_label(int* resident_out) {
-  auto kern = k_label_tile<TH, LabelT, kGiven, kRoots, Src, kXY>;
-  const int smem = kXY ? LabelSmem<TH>::kXYBytes : LabelSmem<TH>::kBytes;
-  static int resident = 0;
-  if (!resident) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+constexpr int kMaxDevices = 64;
+
+// Sets a labelling kernel's shared-memory attributes on the current device
+// and returns how many of its CTAs fit on that device at once.  Function
+// attributes belong to a device, so this is done once per device (and per
+// shared-memory size) and the count is kept per device; call it before any
+// stream capture.
+template <typename Kern>
+cudaError_t configure_on_device(Kern kern, int threads, int smem, int smem_max, std::atomic<int>* resident,
+                                int* resident_out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  int r = resident[dev].load(std::memory_order_acquire);
+  if (!r) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
+    int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TileCta<TH>::kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    cudaGetLastError();
     if (sms <= 0) sms = 152;
     if (per_sm <= 0) per_sm = 1;
-    resident = sms * per_sm;
+    r = sms * per_sm;
+    resident[dev].store(r, std::memory_order_release);
   }
-  if (resident_out) *resident_out = resident;
+  if (resident_out) *resident_out = r;
   return cudaSuccess;
 }
 
+// Shared memory of the Potts labeller for a source: the per-state histogram
+// (q > 4, or any replica batch) needs the larger layout.
+template <int TH, bool kGiven, typename Src>
+int rows_smem(const Src& src) {
+  if constexpr (kGiven) {
+    (void)src;
+    return RowSmem<TH>::kBytesSmallQ;
+  } else if constexpr (Src::kMulti) {
+    (void)src;
+    return RowSmem<TH>::kBytes;
+  } else {
+    return src.b.q > 4 ? RowSmem<TH>::kBytes : RowSmem<TH>::kBytesSmallQ;
+  }
+}
+
+// Potts labeller (k_label_rows): attributes and resident CTAs on this device.
+template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src>
+cudaError_t configure_rows(int smem, int* resident_out) {
+  static std::atomic<int> resident[2][kMaxDevices];
+  const int big = smem > RowSmem<TH>::kBytesSmallQ ? 1 : 0;
+  return configure_on_device(k_label_rows<TH, LabelT, kGiven, kRoots, Src>, RowCta<TH>::kThreads, smem,
+                             RowSmem<TH>::kBytes, resident[big], resident_out);
+}
+
+// XY labeller (k_label_tile<XY>): attributes and resident CTAs on this device.
+template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY>
+cudaError_t configure_tile(int* resident_out) {
+  static std::atomic<int> resident[kMaxDevices];
+  const int smem = kXY ? LabelSmem<TH>::kXYBytes : LabelSmem<TH>::kBytes;
+  return configure_on_device(k_label_tile<TH, LabelT, kGiven, kRoots, Src, kXY>, TileCta<TH>::kThreads, smem,
+                             smem, resident, resident_out);
+}
+
+template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY = false>
+cudaError_t configure_label(const Src& src, int* resident_out) {
+  if constexpr (kXY) {
+    (void)src;
+    return configure_tile<TH, LabelT, kGiven, kRoots, Src, kXY>(resident_out);
+  } else {
+    return configure_rows<TH, LabelT, kGiven, kRoots, Src>(rows_smem<TH, kGiven>(src), resident_out);
+  }
+}
+
+// One labelling launch: a persistent grid of as many tile CTAs as fit.
 template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY = false>
 cudaError_t launch_label_src(const Src& src, uint32_t ntiles, cudaStream_t st) {
-  auto kern = k_label_tile<TH, LabelT, kGiven, kRoots, Src, kXY>;
-  const int smem = kXY ? LabelSmem<TH>::kXYBytes : LabelSmem<TH>::kBytes;
   int resident = 0;
-  cudaError_t e = configure_label<TH, LabelT, kGiven, kRoots, Src, kXY>(&resident);
+  cudaError_t e = configure_label<TH, LabelT, kGiven, kRoots, Src, kXY>(src, &resident);
   if (e != cudaSuccess) return e;
   const uint32_t grid = ntiles < (uint32_t)resident ? ntiles : (uint32_t)resident;
-  kern<<<grid, TileCta<TH>::kThreads, smem, st>>>(src);
+  if (grid == 0) return cudaSuccess;
+  if constexpr (kXY) {
+    k_label_tile<TH, LabelT, kGiven, kRoots, Src, kXY>
+        <<<grid, TileCta<TH>::kThreads, LabelSmem<TH>::kXYBytes, st>>>(src);
+  } else {
+    k_label_rows<TH, LabelT, kGiven, kRoots, Src><<<grid, RowCta<TH>::kThreads, rows_smem<TH, kGiven>(src), st>>>(src);
+  }
   return cudaGetLastError();
 }
 
@@ -99,11 +158,11 @@ cudaError_t sweep_th(uint32_t th, const Src& src, uint32_t ntiles, cudaStream_t 
 }
 
 template <typename LabelT, typename Src>
-cudaError_t configure_th(uint32_t th) {
+cudaError_t configure_th(uint32_t th, const Src& src) {
   switch (th) {
-    case 16: return configure_label<16, LabelT, false, false, Src>(nullptr);
-    case 32: return configure_label<32, LabelT, false, false, Src>(nullptr);
-    case 64: return configure_label<64, LabelT, false, false, Src>(nullptr);
+    case 16: return configure_label<16, LabelT, false, false, Src>(src, nullptr);
+    case 32: return configure_label<32, LabelT, false, false, Src>(src, nullptr);
+    case 64: return configure_label<64, LabelT, false, false, Src>(src, nullptr);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -464,10 +464,13 @@ int wolff_label_setup(sw_wolff* w) {
   if (!e) e = cudaMemsetAsync(b.err, 0, 64, w->stream);
   if (!e) e = cudaMemsetAsync(b.ocnt, 0, nt * 4, w->stream);
   if (!e) {
+    WolffSrc src;
+    src.b = b;
+    src.lat = w->lat;
     switch (th) {
-      case 16: e = configure_label<16, uint32_t, true, true, WolffSrc>(nullptr); break;
-      case 32: e = configure_label<32, uint32_t, true, true, WolffSrc>(nullptr); break;
-      default: e = configure_label<64, uint32_t, true, true, WolffSrc>(nullptr); break;
+      case 16: e = configure_label<16, uint32_t, true, true, WolffSrc>(src, nullptr); break;
+      case 32: e = configure_label<32, uint32_t, true, true, WolffSrc>(src, nullptr); break;
+      default: e = configure_label<64, uint32_t, true, true, WolffSrc>(src, nullptr); break;
     }
   }
   if (!e) e = cudaStreamSynchronize(w->stream);
