@@ -111,12 +111,12 @@ __device__ __forceinline__ uint32_t run_start64(uint64_t m, uint32_t x, uint32_t
   return mm ? c0 + 63u - (uint32_t)__clzll(mm) : c;
 }
 
-// Warp work queue: each lane appends up to 16 of its remaining items (the
+// Warp work queue: each lane appends up to kCap of its remaining items (the
 // set bits of rem, lowest first, as f(bit)) to Q; returns how many the warp
 // queued.  Entries are ordered by lane, each lane's contiguous.
-template <typename Fn>
+template <uint32_t kCap = 16, typename Fn>
 __device__ __forceinline__ uint32_t enqueue16(uint64_t& rem, uint32_t* Q, int lane, Fn f) {
-  const uint32_t cnt = min((uint32_t)__popcll(rem), 16u);
+  const uint32_t cnt = min((uint32_t)__popcll(rem), kCap);
   uint32_t inc = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -539,7 +539,11 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
 
     if (tid < R::kBitWords) b.ebits[(uint64_t)t * R::kBitWords + tid] = cbits[tid];
     // from here to phase F the staging buffer holds the warps' work queues
+    // (512 entries each, or 256 while L2 -- the roots linked by unions, a
+    // bitmap like NR -- is in use behind them)
     uint32_t* Q = reinterpret_cast<uint32_t*>(sp) + warp * kQCap;
+    uint32_t* Q8 = reinterpret_cast<uint32_t*>(sp) + warp * 256;
+    uint32_t* L2 = reinterpret_cast<uint32_t*>(sp) + C::kWarps * 256;
 
     // ================================================= B: vertical unions
     // Each lane looks at the vertical bonds from its row y to the row below
@@ -589,26 +593,76 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
       uint64_t rem = tk & ~first;
       FM[ly * 4 + (c0 >> 5)] = (uint32_t)first;
       FM[ly * 4 + (c0 >> 5) + 1] = (uint32_t)(first >> 32);
+      L2[ly * 4 + (c0 >> 5)] = 0u;
+      L2[ly * 4 + (c0 >> 5) + 1] = 0u;
       __syncthreads();
       volatile uint16_t* vp = P;
-      // top-down: row y+1's first-met runs under the roots of row y
-      for (int y = 0; y + 1 < h; ++y) {
-        for (int x = tid; x < w; x += kThreads) {
-          const int wd = y * 4 + (x >> 5);
-          if ((FM[wd] >> (x & 31)) & 1u) {
-            const uint32_t a = run_start(RS[wd], x & 31, (uint32_t)(x & ~31), RC[wd]);
-            const uint32_t c = run_start(RS[wd + 4], x & 31, (uint32_t)(x & ~31), RC[wd + 4]);
-            vp[(y + 1) * kTW + c] = vp[y * kTW + a];
-            atomicOr(&NR[(y + 1) * 4 + (c >> 5)], 1u << (c & 31u));
+      // top-down, each warp over its own band of kRpw rows (lane l: columns
+      // 4l .. 4l+3): row y+1's first-met runs under the parent of the row-y
+      // run, which is its local root once row y is done; a run of the band's
+      // top row counts as a local root itself, and its own parent in the row
+      // above (where another warp may still be at work) is an ancestor,
+      // resolved by the jumps below and the compression of phase C
+      {
+        const int lx = 4 * lane;
+#pragma unroll 1
+        for (int k = 0; k < kRpw; ++k) {
+          const int y = warp * kRpw - 1 + k;  // the pair (y, y+1), y+1 in the band
+          if (y >= 0 && y + 1 < h) {          // warp-uniform
+            const int wd = y * 4 + (lx >> 5);
+            const uint32_t f4 = (FM[wd] >> (lx & 31)) & 0xFu;
+            if (f4) {
+              const uint32_t sa = RS[wd], sc = RS[wd + 4];
+              const uint32_t ca = RC[wd], cc = RC[wd + 4];
+              const uint32_t cw = (uint32_t)(lx & ~31);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                if ((f4 >> q) & 1u) {
+                  const int b = (lx & 31) + q;
+                  const uint32_t a = y * kTW + run_start(sa, b, cw, ca);
+                  const uint32_t c = (y + 1) * kTW + run_start(sc, b, cw, cc);
+                  // a run of the band's top row is the local root of the
+                  // band's runs below it (its own parent, from the band above,
+                  // may not be final yet)
+                  vp[c] = y == warp * kRpw ? (uint16_t)a : vp[a];
+                  atomicOr(&NR[c >> 5], 1u << (c & 31u));
+                }
+              }
+            }
           }
+          __syncwarp();
         }
-        __syncthreads();
+      }
+      __syncthreads();
+      // the bands' top rows: pointer jumping (every band above resolved in
+      // log2(bands) + 1 rounds), after which every parented start is at most
+      // two links below its root
+      {
+        constexpr int kBands = TH / kRpw;
+        constexpr int kJumps = kBands <= 1 ? 0 : (kBands <= 2 ? 1 : (kBands <= 4 ? 3 : 4));
+        const int yt = warp * kRpw;  // this warp's top row
+        const int lx = 4 * lane;
+#pragma unroll 1
+        for (int r = 0; r < kJumps; ++r) {
+          if (warp > 0 && yt < h) {
+            const int wd = yt * 4 + (lx >> 5);
+            const uint32_t m4 = (RS[wd] & NR[wd]) >> (lx & 31) & 0xFu;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              if ((m4 >> q) & 1u) {
+                const uint32_t sj = (uint32_t)(yt * kTW + lx + q);
+                vp[sj] = vp[vp[sj]];
+              }
+            }
+          }
+          __syncthreads();
+        }
       }
       // the trees joined again by the remaining bonds
       const uint32_t ja = (uint32_t)(ly * kTW), jc = ja + kTW;
       volatile uint32_t* vP32 = reinterpret_cast<volatile uint32_t*>(P);
       for (;;) {
-        const uint32_t nq = enqueue16(rem, Q, lane, [&](uint32_t x) {
+        const uint32_t nq = enqueue16<8>(rem, Q8, lane, [&](uint32_t x) {
           return (ja + run_start64(Sa, x, (uint32_t)c0, Cw[0])) |
                  ((jc + run_start64(S1, x, (uint32_t)c0, c1)) << 16);
         });
@@ -618,7 +672,7 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
         bool act = false;
         for (uint32_t it = 0;; ++it) {
           const bool fetch = !act && idx < nq;
-          const uint32_t e = fetch ? Q[idx] : 0u;
+          const uint32_t e = fetch ? Q8[idx] : 0u;
           idx += fetch ? 32u : 0u;
           a = fetch ? (e & 0xFFFFu) : a;
           c = fetch ? (e >> 16) : c;
@@ -646,6 +700,7 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
             const uint32_t nw = (old & ~(0xFFFFu << sh)) | (lo << sh);
             if (atomicCAS(reinterpret_cast<uint32_t*>(P) + (hi >> 1), old, nw) == old) {
               atomicOr(&NR[hi >> 5], 1u << (hi & 31u));
+              atomicOr(&L2[hi >> 5], 1u << (hi & 31u));
               done = true;
             }
           }
@@ -680,25 +735,31 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
         atomicOr(reinterpret_cast<uint32_t*>(P) + (r >> 1), kMarkA << ((r & 1u) << 4));
       }
     }
-    // every linked run start is pointed straight at its root, so that a
-    // site's code is at most two lookups away in phase F: the lanes queue
-    // their linked starts and walk them in lockstep, two links per
-    // iteration (path splitting on the way)
+    // the roots that unions linked, and the parented starts of the bands'
+    // top rows, are pointed straight at their root: any start then is at
+    // most two links below its root (its parent in the forest, one of these,
+    // and the root), which phase F looks up at once.  The lanes queue these
+    // starts of their rows and walk them in lockstep, two links per
+    // iteration (path splitting on the way).
     {
       volatile uint16_t* vp = P;
       uint64_t rem = 0;
-      if (ly < h)
-        rem = ((uint64_t)Sm[0] & NR[ly * 4 + (c0 >> 5)]) |
-              (((uint64_t)Sm[1] & NR[ly * 4 + (c0 >> 5) + 1]) << 32);
+      if (ly < h) {
+        rem = (uint64_t)L2[ly * 4 + (c0 >> 5)] | ((uint64_t)L2[ly * 4 + (c0 >> 5) + 1] << 32);
+        if (ly == warp * kRpw && warp > 0)  // a band's top row: its parented starts
+          rem |= ((uint64_t)Sm[0] & NR[ly * 4 + (c0 >> 5)]) |
+                 (((uint64_t)Sm[1] & NR[ly * 4 + (c0 >> 5) + 1]) << 32);
+      }
       const uint32_t jb = (uint32_t)(ly * kTW + c0);
+      __syncwarp();
       for (;;) {
-        const uint32_t nq = enqueue16(rem, Q, lane, [&](uint32_t x) { return jb + x; });
+        const uint32_t nq = enqueue16<8>(rem, Q8, lane, [&](uint32_t x) { return jb + x; });
         if (nq == 0) break;  // warp-uniform
         uint32_t idx = (uint32_t)lane, sj = 0, x = 0;  // idle lanes look at entry 0
         bool act = false;
         for (uint32_t it = 0;; ++it) {
           const bool fetch = !act && idx < nq;
-          const uint32_t e = fetch ? Q[idx] : 0u;
+          const uint32_t e = fetch ? Q8[idx] : 0u;
           idx += fetch ? 32u : 0u;
           sj = fetch ? e : sj;
           x = fetch ? e : x;
@@ -708,7 +769,6 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
             bad = 1;
             break;
           }
-          // two links towards the root (a root names itself, maybe flagged)
           const uint32_t p1 = vp[x] & kIdx16;
           const uint32_t p2 = vp[p1] & kIdx16;
           const uint32_t p3 = vp[p2] & kIdx16;
@@ -791,47 +851,44 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
       for (int yy = tid >> 4; yy < h; yy += kThreads / 16) {
         if (cx < w) {
           const uint32_t Sw = RS[yy * 4 + (cx >> 5)];
-          const int sh = cx & 31;
-          const uint32_t s8 = (Sw >> sh) & 0xFFu;
-          const uint32_t jr = (uint32_t)(yy * kTW);
-          uint32_t st = (uint32_t)cx;
-          if (!(s8 & 1u)) {
-            const uint32_t m = Sw & ((1u << sh) - 1u);
-            st = m ? (uint32_t)((cx & ~31) + 31 - __clz(m)) : (uint32_t)RC[yy * 4 + (cx >> 5)];
-          }
+          const uint32_t s8 = (Sw >> (cx & 31)) & 0xFFu;
+          const uint32_t jr = (uint32_t)(yy * kTW), j8 = jr + (uint32_t)cx;
+          // the run start of the group's first site
+          const uint32_t st0 = (s8 & 1u) ? j8 : jr + run_start(Sw, cx & 31, (uint32_t)(cx & ~31), RC[yy * 4 + (cx >> 5)]);
+          // the group's eight entries in one 16-byte load: a start's entry
+          // is its code (a root) or a link towards its root
+          const uint4 E = *reinterpret_cast<const uint4*>(P + j8);
+          const uint32_t ew[4] = {E.x, E.y, E.z, E.w};
           uint32_t cd[8], rt[8];
           // a run start's root is the first entry with a marker on its path:
-          // two levels are looked up for every site at once (non-starts
-          // repeat their left neighbour), deeper paths are walked afterwards
-          auto look = [&](uint32_t j, uint32_t& x, uint32_t& e) {
-            const uint32_t e1 = vp[j];
-            x = (e1 & kMarks) ? j : e1;
-            e = vp[x];
-          };
-          bool deep;
-          {
-            uint32_t x, e;
-            look(jr + st, x, e);
-            deep = !(e & kMarks);
-            rt[0] = x;
-            cd[0] = e;
-          }
-          // the group's own eight entries in one 16-byte load; a start's
-          // entry is its code (a root) or its root's index
-          const uint4 E = *reinterpret_cast<const uint4*>(P + jr + cx);
-          const uint32_t ew[4] = {E.x, E.y, E.z, E.w};
+          // three lookups cover the paths of length two or less, longer
+          // ones are walked afterwards
+          bool deep = false;
 #pragma unroll
-          for (int k = 1; k < 8; ++k) {
+          for (int k = 0; k < 8; ++k) {
+            const uint32_t ek = (ew[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
             const bool sk = (s8 >> k) & 1u;
-            const uint32_t e1 = (ew[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
-            const bool mk = (e1 & kMarks) != 0u;
-            const uint32_t x = mk ? jr + cx + k : e1;
-            const uint32_t e = (sk && !mk) ? (uint32_t)vp[x] : e1;
-            deep = deep || (sk && !(e & kMarks));
-            rt[k] = sk ? x : rt[k - 1];
-            cd[k] = sk ? e : cd[k - 1];
+            if (k == 0 || sk) {
+              uint32_t x = sk ? j8 + k : st0;          // the run start
+              uint32_t e = sk ? ek : (uint32_t)vp[x];  // its entry
+              if (!(e & kMarks)) {
+                x = e;
+                e = vp[x];
+              }
+              if (!(e & kMarks)) {
+                x = e;
+                e = vp[x];
+              }
+              deep = deep || !(e & kMarks);
+              rt[k] = x;
+              cd[k] = e;
+            } else {
+              rt[k] = rt[k - 1];
+              cd[k] = cd[k - 1];
+            }
           }
           if (deep) {  // rare: a start more than two links below its root
+#pragma unroll
             for (int k = 0; k < 8; ++k) {
               if (k == 0 || ((s8 >> k) & 1u)) {
                 uint32_t x = rt[k], e = cd[k];
