@@ -84,9 +84,10 @@ typedef struct {
                            width of the global cluster labels (site indices) */
   double T;             /* temperature in units of J, finite, > 0 */
   uint64_t seed;        /* Philox key */
-  uint32_t tile_h;      /* labelling tile height: 0 = auto, or 16, 32 or 64
-                           (tile width is 128 sites); results do not depend
-                           on it */
+  uint32_t tile_h;      /* labelling tile height: 0 = auto (16 up to L = 32,
+                           32 up to 256, 64 up to 1024, else 128), or 16, 32,
+                           64 or 128 (tile width is 128 sites); results do
+                           not depend on it */
   uint32_t ring;        /* observable ring capacity in configurations,
                            0 = 1024 */
   uint32_t init;        /* SW_INIT_RANDOM or SW_INIT_ZERO */
@@ -220,7 +221,8 @@ typedef struct sw_batch sw_batch;
 
 typedef struct {
   uint32_t R;           /* replicas, >= 1 */
-  uint32_t tile_h;      /* 0 = 64, or 16 / 32 / 64 (one tile height for all) */
+  uint32_t tile_h;      /* 0 = 64, or 16 / 32 / 64 / 128 (one tile height for
+                           all) */
   const uint64_t *L;    /* host arrays of R entries: linear sizes (>= 2) */
   const uint32_t *q;    /*   states (2..255) */
   const double *T;      /*   temperatures (finite, > 0) */
@@ -347,7 +349,7 @@ typedef struct {
   uint32_t label_bits; /* 0 = auto (32 up to L = 32768, else 64), 32, 64 */
   double T;            /* temperature > 0 */
   uint64_t seed;       /* Philox key */
-  uint32_t tile_h;     /* 0 = auto, 16, 32, 64 */
+  uint32_t tile_h;     /* 0 = auto (at most 64), 16, 32, 64 */
   uint32_t ring;       /* configurations whose observables are kept (0 = 1024) */
   uint32_t init;       /* SW_INIT_RANDOM (angles from the init stream) or SW_INIT_ZERO */
   uint32_t measure;    /* 0: measure after every sweep; 2: only on request */

@@ -59,7 +59,8 @@ uint32_t pick_tile_h(uint64_t L, uint32_t requested) {
   if (requested) return requested;
   if (L <= 32) return 16;
   if (L <= 256) return 32;
-  return 64;
+  if (L <= 1024) return 64;
+  return 128;
 }
 
 Lattice make_lattice(uint64_t L, uint32_t th) {
@@ -123,6 +124,7 @@ static cudaError_t label_given_t(uint32_t th, const Bufs& b, const Lattice& lat,
     SWGB_CASE(16)
     SWGB_CASE(32)
     SWGB_CASE(64)
+    SWGB_CASE(128)
 #undef SWGB_CASE
     default:
       return cudaErrorInvalidValue;
@@ -330,6 +332,7 @@ cudaError_t sweep_banded_th(sw_sim* s, const uint32_t* r, uint32_t nb) {
     case 16: return sweep_banded<16, LabelT>(s, r, nb);
     case 32: return sweep_banded<32, LabelT>(s, r, nb);
     case 64: return sweep_banded<64, LabelT>(s, r, nb);
+    case 128: return sweep_banded<128, LabelT>(s, r, nb);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -373,7 +376,7 @@ int sw_create_ex(const sw_params* prm, sw_sim** out) {
   if (lb != 32 && lb != 64) return SW_ERR_INVAL;
   if (lb == 32 && L * L > (1ull << 32)) return SW_ERR_INVAL;
   const uint32_t th = pick_tile_h(L, prm->tile_h);
-  if (th != 16 && th != 32 && th != 64) return SW_ERR_INVAL;
+  if (th != 16 && th != 32 && th != 64 && th != 128) return SW_ERR_INVAL;
   const uint32_t ring = prm->ring ? prm->ring : 1024u;
 
   sw_sim* s = new (std::nothrow) sw_sim();
@@ -769,7 +772,7 @@ int sw_label_bonds(uint64_t L, const uint8_t* bonds, void* roots, uint32_t label
   if (label_bits != 32 && label_bits != 64) return SW_ERR_INVAL;
   if (label_bits == 32 && L * L > (1ull << 32)) return SW_ERR_INVAL;
   const uint32_t th = pick_tile_h(L, tile_h);
-  if (th != 16 && th != 32 && th != 64) return SW_ERR_INVAL;
+  if (th != 16 && th != 32 && th != 64 && th != 128) return SW_ERR_INVAL;
   const Lattice lat = make_lattice(L, th);
   const DeviceAllocator al = current_allocator();
   const uint64_t N = L * L, nt = lat.ntiles;

@@ -152,7 +152,7 @@ int sw_batch_create_ex(const sw_batch_params* p, sw_batch** out) {
   if (!p || !out || p->R == 0 || !p->L || !p->q || !p->T || !p->seed) return SW_ERR_INVAL;
   *out = nullptr;
   const uint32_t th = p->tile_h ? p->tile_h : 64u;
-  if (th != 16 && th != 32 && th != 64) return SW_ERR_INVAL;
+  if (th != 16 && th != 32 && th != 64 && th != 128) return SW_ERR_INVAL;
   if (p->init > SW_INIT_ZERO || p->measure > 2 || p->graph > 2) return SW_ERR_INVAL;
   uint32_t lb = 32;
   for (uint32_t r = 0; r < p->R; ++r) {

@@ -153,6 +153,9 @@ cudaError_t sweep_th(uint32_t th, const Src& src, uint32_t ntiles, cudaStream_t 
     case 16: return sweep_src<16, LabelT, Src, kXY>(src, ntiles, st, ev);
     case 32: return sweep_src<32, LabelT, Src, kXY>(src, ntiles, st, ev);
     case 64: return sweep_src<64, LabelT, Src, kXY>(src, ntiles, st, ev);
+    case 128:
+      if constexpr (!kXY) return sweep_src<128, LabelT, Src, false>(src, ntiles, st, ev);
+      else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }
@@ -163,6 +166,7 @@ cudaError_t configure_th(uint32_t th, const Src& src) {
     case 16: return configure_label<16, LabelT, false, false, Src>(src, nullptr);
     case 32: return configure_label<32, LabelT, false, false, Src>(src, nullptr);
     case 64: return configure_label<64, LabelT, false, false, Src>(src, nullptr);
+    case 128: return configure_label<128, LabelT, false, false, Src>(src, nullptr);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -470,7 +470,8 @@ int wolff_label_setup(sw_wolff* w) {
     switch (th) {
       case 16: e = configure_label<16, uint32_t, true, true, WolffSrc>(src, nullptr); break;
       case 32: e = configure_label<32, uint32_t, true, true, WolffSrc>(src, nullptr); break;
-      default: e = configure_label<64, uint32_t, true, true, WolffSrc>(src, nullptr); break;
+      case 64: e = configure_label<64, uint32_t, true, true, WolffSrc>(src, nullptr); break;
+      default: e = configure_label<128, uint32_t, true, true, WolffSrc>(src, nullptr); break;
     }
   }
   if (!e) e = cudaStreamSynchronize(w->stream);
@@ -491,7 +492,8 @@ cudaError_t wolff_step_label(sw_wolff* w) {
   switch (w->th) {
     case 16: e = wolff_label<16>(w); break;
     case 32: e = wolff_label<32>(w); break;
-    default: e = wolff_label<64>(w); break;
+    case 64: e = wolff_label<64>(w); break;
+    default: e = wolff_label<128>(w); break;
   }
   if (e) return e;
   blocks = (w->N + 255) / 256;

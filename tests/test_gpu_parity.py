@@ -11,7 +11,7 @@ import paper_1208_2080_gb300 as sw
 
 pytestmark = pytest.mark.gpu
 
-TILE_HS = [16, 32, 64]
+TILE_HS = [16, 32, 64, 128]
 
 
 def _torch():
