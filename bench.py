@@ -40,12 +40,12 @@ METRIC = "SW spin updates/ns at q=2, T_c, L=65536 (update + measurement)"
 UNIT = "spin updates/ns"
 PAPER_UPDATE_MEASURE = 33.85  # Table 1, L=65536, 256x Tesla M2050, update + measurement
 # Algorithmic HBM bytes per site moved by each kernel of a sweep in this
-# design: k_label_tile reads the uint8 spin and writes the 16-bit site code;
+# design: k_label_rows reads the uint8 spin and writes the 16-bit site code;
 # k_recolor reads the code and writes the spin.  O(1/tile) halo and edge
 # terms are left out.
-ALG_BYTES_PER_SITE = {"k_label_tile": 3.0, "k_merge+k_resolve": 0.0, "k_recolor": 3.0}
-PHASES = ["k_label_tile", "k_merge+k_resolve", "k_recolor"]
-LAUNCHES_PER_SWEEP = 4  # k_label_tile, k_merge, k_resolve, k_recolor
+ALG_BYTES_PER_SITE = {"k_label_rows": 3.0, "k_merge+k_resolve": 0.0, "k_recolor": 3.0}
+PHASES = ["k_label_rows", "k_merge+k_resolve", "k_recolor"]
+LAUNCHES_PER_SWEEP = 4  # k_label_rows, k_merge, k_resolve, k_recolor
 # XY model (embedded clusters, M angles): the labeller reads the angle and
 # writes the code; the reflection reads code and angle and writes the
 # angle; the measurement reads the angle (halo rows come from L2).
@@ -123,7 +123,7 @@ class ClockSampler:
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for f in ("sw_kernels.cuh", "philox.cuh"):
+    for f in ("sw_kernels.cuh", "sw_label.cuh", "philox.cuh"):
         with open(os.path.join(ROOT, "paper_1208_2080_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -95,7 +95,12 @@ typedef struct {
                            sweep (sw_bonds); costs 0.25 B/site per sweep */
   uint32_t measure;     /* 0 = default (on); 2 = off: sweeps record no
                            observables (update only, Sec. 4 Table 1) */
-  uint32_t reserved[3];
+  uint32_t walk_cap;    /* 0 = default (2^24): bound on the steps of one walk
+                           through the global union-find; a sweep whose walk
+                           runs into it reports SW_ERR_TIMEOUT (sw_sync,
+                           sw_measure) and the handle refuses further work.
+                           A small value is for tests of that path. */
+  uint32_t reserved[2];
 } sw_params;
 
 /* Library-wide device allocator (e.g. a framework's caching allocator).
@@ -408,8 +413,9 @@ int sw_xy_last_error(const sw_xy *xy);
  * ------------------------------------------------------------------------- */
 typedef struct sw_wolff sw_wolff;
 /* init: SW_INIT_RANDOM (the Potts init stream) or SW_INIT_ZERO; ring: steps
- * whose cluster sizes are kept (0 = 1024).  Allocates N spins and an N-slot
- * queue of uint32 site indices. */
+ * whose cluster sizes are kept (0 = 1024).  Allocates N spins, an N-slot
+ * queue of uint32 site indices and the labelling buffers of the default
+ * mode. */
 int sw_wolff_create(uint64_t L, uint32_t q, double T, uint64_t seed,
                     uint32_t init, uint32_t ring, sw_wolff **out);
 /* (Create: SW_ERR_INVAL for L outside 2..32768, q outside 2..255, T <= 0 or
@@ -433,16 +439,24 @@ int sw_wolff_spins(sw_wolff *w, uint8_t *dst, uint64_t n, int dst_on_device);
 int sw_wolff_set_spins(sw_wolff *w, const uint8_t *src, uint64_t n,
                        int src_on_device);
 int sw_wolff_get_step(const sw_wolff *w, uint64_t *step);
-/* How the cluster is found (same result either way).  SW_WOLFF_GROW
- * (default): persistent warps grow it from a site queue, work proportional
- * to the cluster.  SW_WOLFF_LABEL: the step's active bonds over the whole
- * lattice are labelled by the SW sweep's tile union-find and the sites with
- * the seed's root flipped (the connected-component route of the related
- * work); allocates the labelling buffers (about 11 B per site) on first
- * use. */
+/* How the cluster is found (same result either way).  SW_WOLFF_LABEL
+ * (default, tens of times faster on critical clusters): the step's active
+ * bonds over the whole lattice are labelled by the SW sweep's tile
+ * union-find and the sites with the seed's root flipped (the
+ * connected-component route of the related work); its buffers (about 11 B
+ * per site) are taken by sw_wolff_create.  SW_WOLFF_GROW: persistent warps
+ * grow the cluster from a site queue, work proportional to the cluster but
+ * bound by the latency of the growth front; kept as the order-independent
+ * reference form of the step. */
 #define SW_WOLFF_GROW 0
 #define SW_WOLFF_LABEL 1
 int sw_wolff_set_mode(sw_wolff *w, int mode);
+/* Growth mode: the number of idle polls (each followed by a back-off of up to
+ * 1 us) after which a growth warp that finds no work, while the cluster is
+ * not complete, gives up; the step then reports SW_ERR_TIMEOUT (sw_wolff_sync)
+ * and the handle refuses further steps.  0 restores the default (2^22).  A
+ * small value is for tests of that path: no wait of the growth is unbounded. */
+int sw_wolff_set_wait_limit(sw_wolff *w, uint32_t idle_polls);
 
 /* ---------------------------------------------------------------------------
  * Surrogate network (not in the paper): a 3 -> 64 -> 64 -> 64 -> 4 tanh MLP

@@ -43,6 +43,7 @@ EXPORTS = [
     "sw_xy_profile", "sw_xy_profile_read", "sw_xy_last_error",
     "sw_wolff_create", "sw_wolff_destroy", "sw_wolff_bind_stream", "sw_wolff_step", "sw_wolff_sync",
     "sw_wolff_sizes", "sw_wolff_spins", "sw_wolff_set_spins", "sw_wolff_get_step", "sw_wolff_set_mode",
+    "sw_wolff_set_wait_limit",
 ]
 
 
@@ -62,7 +63,7 @@ class sw_params(ctypes.Structure):
                 ("T", ctypes.c_double), ("seed", ctypes.c_uint64), ("tile_h", ctypes.c_uint32),
                 ("ring", ctypes.c_uint32), ("init", ctypes.c_uint32),
                 ("store_bonds", ctypes.c_uint32), ("measure", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 3)]
+                ("walk_cap", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
 
 
 class sw_xy_params(ctypes.Structure):
@@ -184,6 +185,7 @@ def lib():
         "sw_wolff_set_spins": (i32, [vp, vp, u64, i32]),
         "sw_wolff_get_step": (i32, [vp, u64p]),
         "sw_wolff_set_mode": (i32, [vp, i32]),
+        "sw_wolff_set_wait_limit": (i32, [vp, u32]),
         "sw_label_bonds_2stage": (i32, [u64, u64, vp, vp, u32, ctypes.POINTER(ctypes.c_uint32),
                                         ctypes.POINTER(ctypes.c_float), vp]),
     }
@@ -256,7 +258,7 @@ class Sim:
     """One L x L lattice on the GPU (include/sw.h handle)."""
 
     def __init__(self, L, q, T, seed, *, label_bits=0, tile_h=0, ring=0, init="random",
-                 store_bonds=False, measure=True, stream=None):
+                 store_bonds=False, measure=True, walk_cap=0, stream=None):
         if not _allocator_chosen:
             use_torch_allocator()
         p = sw_params()
@@ -265,6 +267,7 @@ class Sim:
         p.init = SW_INIT_ZERO if init == "zero" else SW_INIT_RANDOM
         p.store_bonds = 1 if store_bonds else 0
         p.measure = 0 if measure else 2
+        p.walk_cap = int(walk_cap)
         h = ctypes.c_void_p()
         self._h = None
         check(lib().sw_create_ex(ctypes.byref(p), ctypes.byref(h)), "sw_create_ex")
@@ -500,7 +503,7 @@ class Wolff:
 
     GROW, LABEL = 0, 1
 
-    def __init__(self, L, q, T, seed, *, init="random", ring=0, mode="grow", stream=None):
+    def __init__(self, L, q, T, seed, *, init="random", ring=0, mode="label", stream=None):
         if not _allocator_chosen:
             use_torch_allocator()
         h = ctypes.c_void_p()
@@ -514,6 +517,10 @@ class Wolff:
         if stream is not False:
             self.bind_stream(stream)
         self.set_mode(mode)
+
+    def set_wait_limit(self, idle_polls):
+        """Idle polls of a growth warp before it gives up (0: the default)."""
+        check(lib().sw_wolff_set_wait_limit(self._h, int(idle_polls)), "sw_wolff_set_wait_limit")
 
     def set_mode(self, mode):
         """"grow" (cluster grown from a site queue) or "label" (whole-lattice

@@ -273,7 +273,7 @@ int check_device(sw_sim* s) {
   cudaError_t e = cudaMemcpyAsync(&err, s->b.err, sizeof(err), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e);
-  if (err & (kErrFind | kErrUnion)) return fail(s, SW_ERR_TIMEOUT);
+  if (err & (kErrFind | kErrUnion | kErrLocal)) return fail(s, SW_ERR_TIMEOUT);
   if (err) return fail(s, SW_ERR_DEVICE);
   return SW_OK;
 }
@@ -421,6 +421,7 @@ int sw_create_ex(const sw_params* prm, sw_sim** out) {
   b.q = s->q;
   b.ring_cap = ring;
   b.measure = s->measure_on ? 1u : 0u;
+  b.walk_cap = prm->walk_cap;
 
   cudaError_t e = cudaSuccess;
   if (!e) e = cudaMemsetAsync(b.T, 0, s->N * (lb / 8), s->stream);
@@ -813,7 +814,7 @@ int sw_label_bonds(uint64_t L, const uint8_t* bonds, void* roots, uint32_t label
     if (e != cudaSuccess) {
       cudaGetLastError();
       rc = SW_ERR_CUDA;
-    } else if (err & (kErrFind | kErrUnion)) {
+    } else if (err & (kErrFind | kErrUnion | kErrLocal)) {
       rc = SW_ERR_TIMEOUT;
     } else if (err) {
       rc = SW_ERR_DEVICE;

@@ -77,7 +77,7 @@ int check_err(sw_batch* b) {
   cudaError_t e = cudaMemcpyAsync(&err, b->err, sizeof(err), cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bcuda(b, e);
-  if (err & (kErrFind | kErrUnion)) return bfail(b, SW_ERR_TIMEOUT);
+  if (err & (kErrFind | kErrUnion | kErrLocal)) return bfail(b, SW_ERR_TIMEOUT);
   if (err) return bfail(b, SW_ERR_DEVICE);
   return SW_OK;
 }

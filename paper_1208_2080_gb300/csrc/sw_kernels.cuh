@@ -132,6 +132,7 @@ struct Bufs {
   uint32_t ring_cap;
   uint32_t measure;           // 1: k_label_tile accumulates observables of its input
   uint32_t rk[20];            // Philox round keys of `seed` (see set_round_keys)
+  uint32_t walk_cap;          // bound on a global union-find walk (0: kFindCap)
   // XY model (embedded clusters, M angles; q = 2 coins): 0 for Potts
   uint32_t M;
   const uint32_t* tt;         // bond thresholds by |sigma| fold indices (c >= d): tt[c(c+1)/2 + d]
@@ -355,8 +356,8 @@ __device__ __forceinline__ uint64_t atomic_min_label(uint64_t* p, uint64_t v) {
 // Root of x with path halving.  The halving stores only ever replace a
 // parent by one of its ancestors, so they cannot undo a concurrent link.
 template <typename LabelT>
-__device__ __forceinline__ LabelT find_global(LabelT* T, LabelT x, uint32_t* err) {
-  for (uint32_t it = 0; it < kFindCap; ++it) {
+__device__ __forceinline__ LabelT find_global(LabelT* T, LabelT x, uint32_t* err, uint32_t cap = kFindCap) {
+  for (uint32_t it = 0; it < cap; ++it) {
     const LabelT p = ldcg(T + x);
     if (p == x) return x;
     const LabelT gp = ldcg(T + p);
@@ -370,8 +371,9 @@ __device__ __forceinline__ LabelT find_global(LabelT* T, LabelT x, uint32_t* err
 
 // find_global with the first parent p = T[x] already loaded.
 template <typename LabelT>
-__device__ __forceinline__ LabelT find_global_from(LabelT* T, LabelT x, LabelT p, uint32_t* err) {
-  for (uint32_t it = 0; it < kFindCap; ++it) {
+__device__ __forceinline__ LabelT find_global_from(LabelT* T, LabelT x, LabelT p, uint32_t* err,
+                                                   uint32_t cap = kFindCap) {
+  for (uint32_t it = 0; it < cap; ++it) {
     if (p == x) return x;
     const LabelT gp = ldcg(T + p);
     if (gp == p) return p;
@@ -384,13 +386,13 @@ __device__ __forceinline__ LabelT find_global_from(LabelT* T, LabelT x, LabelT p
 }
 
 template <typename LabelT>
-__device__ __forceinline__ void unite_global(LabelT* T, LabelT a, LabelT b, uint32_t* err) {
-  for (uint32_t it = 0; it < kFindCap; ++it) {
+__device__ __forceinline__ void unite_global(LabelT* T, LabelT a, LabelT b, uint32_t* err, uint32_t cap = kFindCap) {
+  for (uint32_t it = 0; it < cap; ++it) {
     // both first parents in flight at once: the common case (two roots, or
     // one step from them) costs one round trip instead of two
     const LabelT pa = ldcg(T + a), pb = ldcg(T + b);
-    a = find_global_from(T, a, pa, err);
-    b = find_global_from(T, b, pb, err);
+    a = find_global_from(T, a, pa, err, cap);
+    b = find_global_from(T, b, pb, err, cap);
     if (a == b) return;
     if (a < b) {
       const LabelT tmp = a;
@@ -1107,7 +1109,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__
   // per distinct (a, c) pair does the union
   const unsigned same = __match_any_sync(0xFFFFFFFFu, a) & __match_any_sync(0xFFFFFFFFu, c);
   if (active && (int)(threadIdx.x & 31) == __ffs(same) - 1)
-    unite_global(reinterpret_cast<LabelT*>(b.T), a, c, b.err);
+    unite_global(reinterpret_cast<LabelT*>(b.T), a, c, b.err, b.walk_cap ? b.walk_cap : kFindCap);
 
   if (g < src.ntiles() && t == 0 && pos == 0) {
     const unsigned long long s = b.ctl[0];
@@ -1148,7 +1150,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_resolve(const __grid_constant
   const uint32_t sweep = (uint32_t)b.ctl[1];
   for (uint32_t k = lane; k < n; k += 32) {
     const uint32_t l = b.olist[(uint64_t)t * R::kOpenCap + k];
-    const LabelT r = find_global(T, (LabelT)global_index(lat, x0, y0, l), b.err);
+    const LabelT r = find_global(T, (LabelT)global_index(lat, x0, y0, l), b.err, b.walk_cap ? b.walk_cap : kFindCap);
     b.nso[(uint64_t)t * R::kOpenCap + k] =
         (uint8_t)pick_state(stream4_rk(b.rk, (uint64_t)r, sweep, kDomSpin).x, b.q);
   }
@@ -1245,7 +1247,7 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const __grid_constant__ Sr
               roots[gi + k] = (LabelT)global_index(lat, x0, y0, c[k] & kIdx);
             } else {
               const uint64_t g = global_index(lat, x0, y0, ol[c[k]]);
-              roots[gi + k] = find_global(T, (LabelT)g, b.err);
+              roots[gi + k] = find_global(T, (LabelT)g, b.err, b.walk_cap ? b.walk_cap : kFindCap);
             }
           }
         }

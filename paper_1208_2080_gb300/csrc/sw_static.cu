@@ -131,7 +131,7 @@ extern "C" int sw_label_bonds_static(uint64_t L, const uint8_t* bonds, uint32_t*
     cudaGetLastError();
     return SW_ERR_CUDA;
   }
-  if (err & (kErrFind | kErrUnion)) return SW_ERR_TIMEOUT;
+  if (err & (kErrFind | kErrUnion | kErrLocal)) return SW_ERR_TIMEOUT;
   if (err) return SW_ERR_DEVICE;
   return SW_OK;
 }

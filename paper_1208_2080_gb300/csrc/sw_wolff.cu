@@ -66,6 +66,7 @@ struct WolffArgs {
   uint32_t L, q, thr, ring;
   uint64_t N, bp;
   uint32_t rk[20];
+  uint32_t idle_cap;          // growth mode: idle polls of one warp before it gives up
 };
 
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(kGrowThreads) k_wolff_grow(const __grid_consta
         done = (p == tl) ? 1u : 0u;
       }
       if (__shfl_sync(kFull, done, 0)) return;
-      if (++idle >= kIdleCap) {
+      if (++idle >= a.idle_cap) {
         if (lane == 0) atomicOr(&c->err, kErrWolffTimeout);
         return;
       }
@@ -269,7 +270,7 @@ struct WolffSrc : SingleSrc {};
 
 struct sw_wolff {
   uint64_t L = 0, N = 0;
-  int mode = SW_WOLFF_GROW;
+  int mode = SW_WOLFF_LABEL;
   uint32_t th = 64;
   Lattice lat{};
   Bufs lb{};  // labelling buffers (labelling mode)
@@ -311,7 +312,7 @@ int wcheck(sw_wolff* w) {
   if (!e && w->a.roots) e = cudaMemcpyAsync(&lerr, w->lb.err, 4, cudaMemcpyDeviceToHost, w->stream);
   if (!e) e = cudaStreamSynchronize(w->stream);
   if (e) return wcuda(w);
-  if ((err & kErrWolffTimeout) || (lerr & (kErrFind | kErrUnion))) return w->last_err = SW_ERR_TIMEOUT;
+  if ((err & kErrWolffTimeout) || (lerr & (kErrFind | kErrUnion | kErrLocal))) return w->last_err = SW_ERR_TIMEOUT;
   if (err || lerr) return w->last_err = SW_ERR_DEVICE;
   return SW_OK;
 }
@@ -332,6 +333,8 @@ __global__ void k_wolff_init(uint8_t* s, uint64_t N, uint32_t q, const __grid_co
     s[i] = (uint8_t)pick_state(v[i & 3], q);
   }
 }
+
+int wolff_label_setup(sw_wolff* w);
 
 }  // namespace
 
@@ -366,6 +369,7 @@ int sw_wolff_create(uint64_t L, uint32_t q, double T, uint64_t seed, uint32_t in
   a.N = w->N;
   a.q = q;
   a.thr = bond_threshold(T);
+  a.idle_cap = kIdleCap;
   a.ring = w->ring;
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   for (int r = 0; r < 10; ++r) {
@@ -399,6 +403,13 @@ int sw_wolff_create(uint64_t L, uint32_t q, double T, uint64_t seed, uint32_t in
     wrelease(w);
     delete w;
     return SW_ERR_CUDA;
+  }
+  // the labelling mode is the default: its buffers are taken now
+  const int rc = wolff_label_setup(w);
+  if (rc) {
+    wrelease(w);
+    delete w;
+    return rc;
   }
   *out = w;
   return SW_OK;
@@ -506,6 +517,12 @@ cudaError_t wolff_step_label(sw_wolff* w) {
 }  // namespace
 
 extern "C" {
+
+int sw_wolff_set_wait_limit(sw_wolff* w, uint32_t idle_polls) {
+  if (!w) return SW_ERR_INVAL;
+  w->a.idle_cap = idle_polls ? idle_polls : kIdleCap;
+  return SW_OK;
+}
 
 int sw_wolff_set_mode(sw_wolff* w, int mode) {
   if (!w || (mode != SW_WOLFF_GROW && mode != SW_WOLFF_LABEL)) return SW_ERR_INVAL;

@@ -215,7 +215,7 @@ int xcheck(sw_xy* s) {
   cudaError_t e = cudaMemcpyAsync(&err, s->b.err, sizeof(err), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return xcuda(s);
-  if (err & (kErrFind | kErrUnion)) return xfail(s, SW_ERR_TIMEOUT);
+  if (err & (kErrFind | kErrUnion | kErrLocal)) return xfail(s, SW_ERR_TIMEOUT);
   if (err) return xfail(s, SW_ERR_DEVICE);
   return SW_OK;
 }

@@ -52,7 +52,7 @@ def test_critical_run_against_oracle(mode):
 
 def test_modes_agree_and_can_be_switched():
     L, q, T = 300, 2, sw.tc(2)
-    with sw.Wolff(L, q, T, 5) as a, sw.Wolff(L, q, T, 5, mode="label") as b:
+    with sw.Wolff(L, q, T, 5, mode="grow") as a, sw.Wolff(L, q, T, 5) as b:
         a.step(10)
         b.step(10)
         a.set_mode("label")
@@ -62,6 +62,15 @@ def test_modes_agree_and_can_be_switched():
         assert np.array_equal(a.spins(), b.spins())
         assert np.array_equal(a.sizes(0, 20), b.sizes(0, 20))
         a.sync()
+        b.sync()
+
+
+def test_label_mode_is_the_default():
+    with sw.Wolff(64, 2, sw.tc(2), 9) as d, sw.Wolff(64, 2, sw.tc(2), 9, mode="label") as b:
+        d.step(5)
+        b.step(5)
+        assert np.array_equal(d.spins(), b.spins())
+        d.sync()
         b.sync()
 
 

@@ -25,7 +25,11 @@ def _call_static(L, packed, roots, tile_h=0):
 
 def test_static_labelling_matches_allocating_entry_point_twice():
     import torch
-    cases = [(1024, 0.58, 7, 0), (300, 0.5, 8, 16)]  # two calls in a row, different sizes
+    # calls in a row on the one shared array: different sizes, the largest
+    # layouts it holds (L = 1024 with 16- and 32-row tiles), an odd L (rows
+    # not 4-byte aligned), and the same L again with another bond lattice
+    cases = [(1024, 0.58, 7, 0), (300, 0.5, 8, 16), (1024, 0.5, 9, 16), (1024, 0.52, 10, 32),
+             (1023, 0.55, 11, 0), (1023, 0.2, 12, 0)]
     for L, density, seed, th in cases:
         b = synth.random_bonds(L, density, seed)
         packed = torch.from_numpy(sw.pack_bonds(b).reshape(-1).copy()).cuda()
