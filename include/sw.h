@@ -81,7 +81,12 @@ typedef struct {
   uint64_t L;           /* linear size, >= 2 (N = L*L sites) */
   uint32_t q;           /* states, 2..255 */
   uint32_t label_bits;  /* 0 = auto (32 if L <= 32768, else 64), 32 or 64:
-                           width of the global cluster labels (site indices) */
+                           width of the cluster labels (site indices) where
+                           they are written out; 32 requires L*L <= 2^32.
+                           Inside a sweep the labels are the site keys of
+                           the global union-find's 64-bit nodes (one per
+                           open tile root, 8 B x (2 tile_h + 256) per tile),
+                           whatever this width */
   double T;             /* temperature in units of J, finite, > 0 */
   uint64_t seed;        /* Philox key */
   uint32_t tile_h;      /* labelling tile height: 0 = auto (16 up to L = 32,
@@ -364,8 +369,8 @@ typedef struct {
  * clamped to 2^32 - 1, into tt[c * (M/2+1) + d] (host array of
  * (M/2+1)^2 entries; M/2 rounded down).  Host only. */
 int sw_xy_thresholds(uint32_t M, double T, uint32_t *tt);
-/* Allocates the lattice (N bytes), the per-site codes (2N), the label
- * table (4N or 8N bytes, sparse use), per-tile records and the ring through
+/* Allocates the lattice (N bytes), the per-site codes (2N), the global
+ * union-find (8 B per possible open tile root), per-tile records and the ring through
  * the installed allocator; uploads the threshold table; measures the
  * initial configuration (measure = 0).  SW_ERR_INVAL for parameters out of
  * range (label_bits 32 with L*L > 2^32 included), SW_ERR_NOMEM, SW_ERR_CUDA.

@@ -72,6 +72,13 @@ Lattice make_lattice(uint64_t L, uint32_t th) {
   lat.vec4 = (L % 4 == 0) ? 1u : 0u;
   lat.ntiles = lat.ntx * lat.nty;
   lat.ntx_m = lat.ntx == 1 ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / lat.ntx);
+  lat.xb = 0;
+  while ((1ull << lat.xb) < L) ++lat.xb;
+  // node words carry the node index when key and node fit in 64 bits
+  const uint64_t nodes = (uint64_t)lat.ntiles * open_cap(th);
+  lat.db = 1;
+  while ((1ull << lat.db) < nodes) ++lat.db;
+  if (2 * lat.xb + lat.db > 64) lat.db = 0;
   return lat;
 }
 
@@ -87,11 +94,6 @@ static cudaError_t launch_label_t(const Bufs& b, const Lattice& lat, cudaStream_
 template <int TH, typename LabelT>
 static cudaError_t launch_merge_t(const Bufs& b, const Lattice& lat, cudaStream_t st) {
   return launch_merge_src<TH, LabelT>(SingleSrc{b, lat}, lat.ntiles, st);
-}
-
-template <int TH, typename LabelT>
-static cudaError_t launch_resolve_t(const Bufs& b, const Lattice& lat, cudaStream_t st) {
-  return launch_resolve_src<TH, LabelT>(SingleSrc{b, lat}, lat.ntiles, st);
 }
 
 template <int TH, typename LabelT, bool kRoots>
@@ -399,18 +401,17 @@ int sw_create_ex(const sw_params* prm, sw_sim** out) {
   b.spin = (uint8_t*)take(s, s->N + 16);
   b.code = (uint16_t*)take(s, s->N * 2 + 16);
   b.bonds = prm->store_bonds ? (uint8_t*)take(s, L * s->lat.bp + 16) : nullptr;
-  b.T = take(s, s->N * (lb / 8));
+  b.G = (uint64_t*)take(s, nt * open_cap(th) * 8);
   b.edge = (uint16_t*)take(s, nt * edge_u16(th) * 2);
   b.ebits = (uint32_t*)take(s, nt * bit_words(th) * 4);
-  b.olist = (uint16_t*)take(s, nt * open_cap(th) * 2);
   b.ocnt = (uint32_t*)take(s, nt * 4);
   b.nso = (uint8_t*)take(s, nt * open_cap(th));
   b.acc = (unsigned long long*)take(s, 8 * 260);
   b.ring = (unsigned long long*)take(s, (size_t)ring * (2 + s->q) * 8);
   b.ctl = (unsigned long long*)take(s, 64);
   b.err = (uint32_t*)take(s, 64);
-  if (!b.spin || !b.code || (prm->store_bonds && !b.bonds) || !b.T || !b.edge || !b.ebits ||
-      !b.olist || !b.ocnt || !b.nso || !b.acc || !b.ring || !b.ctl || !b.err) {
+  if (!b.spin || !b.code || (prm->store_bonds && !b.bonds) || !b.G || !b.edge || !b.ebits ||
+      !b.ocnt || !b.nso || !b.acc || !b.ring || !b.ctl || !b.err) {
     release_all(s);
     delete s;
     return SW_ERR_NOMEM;
@@ -424,7 +425,7 @@ int sw_create_ex(const sw_params* prm, sw_sim** out) {
   b.walk_cap = prm->walk_cap;
 
   cudaError_t e = cudaSuccess;
-  if (!e) e = cudaMemsetAsync(b.T, 0, s->N * (lb / 8), s->stream);
+  if (!e) e = cudaMemsetAsync(b.G, 0, nt * open_cap(th) * 8, s->stream);
   if (!e) e = cudaMemsetAsync(b.acc, 0, 8 * 260, s->stream);
   if (!e) e = cudaMemsetAsync(b.ring, 0xFF, (size_t)ring * (2 + s->q) * 8, s->stream);
   if (!e) e = cudaMemsetAsync(b.ctl, 0, 64, s->stream);
@@ -788,10 +789,9 @@ int sw_label_bonds(uint64_t L, const uint8_t* bonds, void* roots, uint32_t label
   Bufs b{};
   b.bonds = const_cast<uint8_t*>(bonds);
   b.code = (uint16_t*)get(N * 2 + 16);
-  b.T = get(N * (label_bits / 8));
+  b.G = (uint64_t*)get(nt * open_cap(th) * 8);
   b.edge = (uint16_t*)get(nt * edge_u16(th) * 2);
   b.ebits = (uint32_t*)get(nt * bit_words(th) * 4);
-  b.olist = (uint16_t*)get(nt * open_cap(th) * 2);
   b.ocnt = (uint32_t*)get(nt * 4);
   b.ctl = (unsigned long long*)get(64);
   b.err = (uint32_t*)get(64);
@@ -799,12 +799,12 @@ int sw_label_bonds(uint64_t L, const uint8_t* bonds, void* roots, uint32_t label
   b.measure = 0;
   int rc = SW_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  if (!b.code || !b.T || !b.edge || !b.ebits || !b.olist || !b.ocnt || !b.ctl || !b.err) {
+  if (!b.code || !b.G || !b.edge || !b.ebits || !b.ocnt || !b.ctl || !b.err) {
     rc = SW_ERR_NOMEM;
   } else {
     cudaError_t e = cudaMemsetAsync(b.ctl, 0, 64, st);
     if (!e) e = cudaMemsetAsync(b.err, 0, 64, st);
-    if (!e) e = cudaMemsetAsync(b.T, 0, N * (label_bits / 8), st);
+    if (!e) e = cudaMemsetAsync(b.G, 0, nt * open_cap(th) * 8, st);
     if (!e)
       e = label_bits == 64 ? label_given_t<uint64_t>(th, b, lat, (uint64_t*)roots, st)
                            : label_given_t<uint32_t>(th, b, lat, (uint32_t*)roots, st);

@@ -183,8 +183,8 @@ int sw_batch_create_ex(const sw_batch_params* p, sw_batch** out) {
     const Lattice lat = make_lattice(L, th);
     const uint64_t nt = lat.ntiles;
     off[r] = bytes;
-    bytes += up256(N + 16) + up256(2 * N + 16) + up256(N * (lb / 8)) + up256(nt * edge_u16(th) * 2) +
-             up256(nt * bit_words(th) * 4) + up256(nt * open_cap(th) * 2) + up256(nt * 4) +
+    bytes += up256(N + 16) + up256(2 * N + 16) + up256(nt * open_cap(th) * 8) + up256(nt * edge_u16(th) * 2) +
+             up256(nt * bit_words(th) * 4) + up256(nt * 4) +
              up256(nt * open_cap(th)) + up256(8 * 260) + up256((size_t)b->ring * (2 + p->q[r]) * 8) +
              up256(64);
     total += nt;
@@ -220,10 +220,9 @@ int sw_batch_create_ex(const sw_batch_params* p, sw_batch** out) {
     memset(&bb, 0, sizeof(bb));
     bb.spin = c; c += up256(N + 16);
     bb.code = (uint16_t*)c; c += up256(2 * N + 16);
-    bb.T = c; c += up256(N * (lb / 8));
+    bb.G = (uint64_t*)c; c += up256(nt * open_cap(th) * 8);
     bb.edge = (uint16_t*)c; c += up256(nt * edge_u16(th) * 2);
     bb.ebits = (uint32_t*)c; c += up256(nt * bit_words(th) * 4);
-    bb.olist = (uint16_t*)c; c += up256(nt * open_cap(th) * 2);
     bb.ocnt = (uint32_t*)c; c += up256(nt * 4);
     bb.nso = c; c += up256(nt * open_cap(th));
     bb.acc = (unsigned long long*)c; c += up256(8 * 260);

@@ -16,15 +16,14 @@
 //       here (Sec. 2 step (3)), drawn once per cluster from their root =
 //       smallest site index.  Per site it writes a 16-bit code: 0x8000|state
 //       for a closed cluster, the slot of its open root otherwise.  For the
-//       boundary pass it writes the local roots of the four edge lines, the
-//       cross-edge bond bits, the list of open local roots, and initialises
-//       their global labels.
+//       boundary pass it writes the open slots of the four edge lines, the
+//       cross-edge bond bits, and initialises the open roots' nodes of the
+//       global union-find (below).
 //   k_merge       Sec. 2 step (2), global part: the single-GPU analogue of
 //       the paper's boundary-only inter-GPU labelling (Sec. 3): for every
 //       active bond that crosses a tile edge (periodic wrap included) a
-//       lock-free atomicMin union of the two open roots' global labels
-//       (site indices, uint32 or uint64), lanes that would repeat the same
-//       union are merged with __match_any_sync.
+//       lock-free atomicMin union of the two open roots' nodes; lanes that
+//       would repeat the same union are merged with __match_any_sync.
 //   k_resolve     Sec. 2 step (3) for open clusters: each open local root
 //       finds (and compresses to) its global root and draws the cluster
 //       state.
@@ -111,16 +110,17 @@ struct Lattice {
   uint32_t vec4;      // L % 4 == 0: rows start 4-byte aligned
   uint32_t ntiles;
   uint32_t ntx_m;     // floor(2^32 / ntx) (2^32 - 1 for ntx = 1): t / ntx by a multiply
+  uint32_t xb;        // bits of a column index: the least b with 2^b >= L
+  uint32_t db;        // bits of a global union-find node index, 0: nodes named by open slot
 };
 
 struct Bufs {
   uint8_t* spin;              // N spins
   uint16_t* code;             // N per-site codes
   uint8_t* bonds;             // packed bonds (out, or in for the given-bond mode) or null
-  void* T;                    // N global labels (LabelT); only open roots are touched
-  uint16_t* edge;             // ntiles * kEdge
+  uint64_t* G;                // ntiles * kOpenCap nodes of the global union-find
+  uint16_t* edge;             // ntiles * kEdge open slots of the edge sites
   uint32_t* ebits;            // ntiles * kBitWords
-  uint16_t* olist;            // ntiles * kOpenCap
   uint32_t* ocnt;             // ntiles
   uint8_t* nso;               // ntiles * kOpenCap: new state of each open root
   unsigned long long* acc;    // [1 + q]: E_sat, n[q] of the configuration being measured
@@ -337,71 +337,95 @@ __device__ __forceinline__ uint32_t warp_enqueue(uint16_t* q, uint32_t mask, uin
 }
 
 // ---------------------------------------------------------------- global union-find
-template <typename LabelT>
-__device__ __forceinline__ LabelT ldcg(const LabelT* p);
-template <>
-__device__ __forceinline__ uint32_t ldcg<uint32_t>(const uint32_t* p) {
-  return __ldcg(p);
+// The nodes are the open local roots of all tiles, in a dense table G:
+// node d = t * kOpenCap + slot (slot: the root's place in its tile's open
+// list).  A node's 64-bit word names its parent by the parent's site key
+// and the parent's node,
+//     word = key << db | d,   key = y << xb | x for site (x, y),
+// db the bits of a node index, so a root's word names itself.  Keys order
+// like site indices (row-major), so an atomicMin of whole words links the
+// larger root under the smaller and every cluster's final root is its
+// smallest site index -- the Hoshen-Kopelman label of Sec. 2 -- whatever
+// order the unions run in.  A tile's nodes are contiguous, so the nodes
+// that neighbouring edge sites and one tile's open roots touch share
+// sectors, and the table holds 8 B x open slots instead of a label per site.
+// Where key and node do not fit in 64 bits together (L above 2^17 with
+// small tiles) the word carries the parent's open slot instead (db = 0,
+// word = key << kSlotBits | slot) and the node is computed from the key.
+constexpr int kSlotBits = 9;  // kOpenCap <= 512 for tiles up to 128 x 128
+constexpr uint64_t kSlotMask = (1ull << kSlotBits) - 1;
+
+// Word of node d, the tile-local site `local` of the tile at (x0, y0) whose
+// open slot is `slot`.
+__device__ __forceinline__ uint64_t gword(const Lattice& lat, uint64_t d, uint64_t x0, uint64_t y0, uint32_t local,
+                                          uint32_t slot) {
+  const uint64_t key = ((y0 + (local >> 7)) << lat.xb) | (x0 + (local & (kTW - 1)));
+  return lat.db ? (key << lat.db) | d : (key << kSlotBits) | slot;
 }
-template <>
-__device__ __forceinline__ uint64_t ldcg<uint64_t>(const uint64_t* p) {
+
+// The node a word names.
+template <int TH>
+__device__ __forceinline__ uint64_t gnode(const Lattice& lat, uint64_t w) {
+  if (lat.db) return w & ((1ull << lat.db) - 1);
+  const uint64_t key = w >> kSlotBits;
+  const uint32_t y = (uint32_t)(key >> lat.xb), x = (uint32_t)(key & ((1ull << lat.xb) - 1));
+  return ((uint64_t)(y / (uint32_t)TH) * lat.ntx + (x >> 7)) * (uint64_t)TileRec<TH>::kOpenCap + (w & kSlotMask);
+}
+
+// Site index of the node a word names (the cluster label of a root's word).
+__device__ __forceinline__ uint64_t gsite(const Lattice& lat, uint64_t w) {
+  const uint64_t key = w >> (lat.db ? lat.db : kSlotBits);
+  return (key >> lat.xb) * lat.L + (key & ((1ull << lat.xb) - 1));
+}
+
+// A load that bypasses L1 (another SM may have changed the word).
+__device__ __forceinline__ uint64_t ldcg(const uint64_t* p) {
   return (uint64_t)__ldcg(reinterpret_cast<const unsigned long long*>(p));
 }
 
-__device__ __forceinline__ uint32_t atomic_min_label(uint32_t* p, uint32_t v) { return atomicMin(p, v); }
-__device__ __forceinline__ uint64_t atomic_min_label(uint64_t* p, uint64_t v) {
-  return (uint64_t)atomicMin(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
-}
-
-// Root of x with path halving.  The halving stores only ever replace a
-// parent by one of its ancestors, so they cannot undo a concurrent link.
-template <typename LabelT>
-__device__ __forceinline__ LabelT find_global(LabelT* T, LabelT x, uint32_t* err, uint32_t cap = kFindCap) {
+// Root word of node d, whose word w = G[d] is already loaded, with path
+// halving.  The halving stores only ever replace a parent by one of its
+// ancestors, so they cannot undo a concurrent link.
+template <int TH>
+__device__ __forceinline__ uint64_t gfind(uint64_t* G, const Lattice& lat, uint64_t d, uint64_t w, uint32_t* err,
+                                          uint32_t cap) {
   for (uint32_t it = 0; it < cap; ++it) {
-    const LabelT p = ldcg(T + x);
-    if (p == x) return x;
-    const LabelT gp = ldcg(T + p);
-    if (gp == p) return p;
-    T[x] = gp;
-    x = gp;
+    const uint64_t p = gnode<TH>(lat, w);
+    if (p == d) return w;
+    const uint64_t wp = ldcg(G + p);
+    const uint64_t gp = gnode<TH>(lat, wp);
+    if (gp == p) return wp;
+    G[d] = wp;
+    d = gp;
+    w = ldcg(G + d);
   }
   atomicOr(err, kErrFind);
-  return x;
+  return w;
 }
 
-// find_global with the first parent p = T[x] already loaded.
-template <typename LabelT>
-__device__ __forceinline__ LabelT find_global_from(LabelT* T, LabelT x, LabelT p, uint32_t* err,
-                                                   uint32_t cap = kFindCap) {
+// Union of the clusters of nodes a and c: the larger root is linked under
+// the smaller by an atomicMin of its word; a root that was linked meanwhile
+// (the old word is not its own) is united again from its new parent.
+template <int TH>
+__device__ __forceinline__ void gunite(uint64_t* G, const Lattice& lat, uint64_t a, uint64_t c, uint32_t* err,
+                                       uint32_t cap) {
   for (uint32_t it = 0; it < cap; ++it) {
-    if (p == x) return x;
-    const LabelT gp = ldcg(T + p);
-    if (gp == p) return p;
-    T[x] = gp;
-    x = gp;
-    p = ldcg(T + x);
-  }
-  atomicOr(err, kErrFind);
-  return x;
-}
-
-template <typename LabelT>
-__device__ __forceinline__ void unite_global(LabelT* T, LabelT a, LabelT b, uint32_t* err, uint32_t cap = kFindCap) {
-  for (uint32_t it = 0; it < cap; ++it) {
-    // both first parents in flight at once: the common case (two roots, or
+    // both first words in flight at once: the common case (two roots, or
     // one step from them) costs one round trip instead of two
-    const LabelT pa = ldcg(T + a), pb = ldcg(T + b);
-    a = find_global_from(T, a, pa, err, cap);
-    b = find_global_from(T, b, pb, err, cap);
-    if (a == b) return;
-    if (a < b) {
-      const LabelT tmp = a;
-      a = b;
-      b = tmp;
+    const uint64_t wa = ldcg(G + a), wc = ldcg(G + c);
+    uint64_t ra = gfind<TH>(G, lat, a, wa, err, cap);
+    uint64_t rc = gfind<TH>(G, lat, c, wc, err, cap);
+    if (ra == rc) return;
+    if (ra < rc) {
+      const uint64_t tmp = ra;
+      ra = rc;
+      rc = tmp;
     }
-    const LabelT old = atomic_min_label(T + a, b);
-    if (old == a) return;
-    a = old;
+    const uint64_t na = gnode<TH>(lat, ra);
+    const uint64_t old = (uint64_t)atomicMin(reinterpret_cast<unsigned long long*>(G + na), (unsigned long long)rc);
+    if (old == ra) return;
+    a = gnode<TH>(lat, old);
+    c = gnode<TH>(lat, rc);
   }
   atomicOr(err, kErrUnion);
 }
@@ -621,7 +645,6 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     const bool measure = !kGiven && !kXY && b.measure;
     const uint32_t sweep = kGiven ? 0u : (uint32_t)b.ctl[0];
     const uint32_t qs = q_states <= 4 ? q_states - 1 : 0;  // states counted in registers
-    LabelT* T = reinterpret_cast<LabelT*>(b.T);
     uint64_t x0, y0;
     int w, h;
     tile_geom(lat, t, TH, x0, y0, w, h);
@@ -966,7 +989,8 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
     }
     // ---- open roots get a block of slots in the tile's open list (in
     // whatever order the warps arrive: a slot only names the root to later
-    // kernels, results do not depend on it) and a global label
+    // kernels, results do not depend on it) and their node of the global
+    // union-find, a root for now
     {
       uint32_t obase = 0;
       if (lane == 0 && nopen) obase = atomicAdd(&wcnt[0], nopen);
@@ -974,12 +998,11 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
       for (uint32_t i = lane; i < nopen; i += 32) {
         const uint32_t j = wl[kRegion - 1 - i];
         const uint32_t slot = obase + i;
-        b.olist[(uint64_t)t * R::kOpenCap + slot] = (uint16_t)j;
         // the high half is the site code (the slot); the labelling-only form
         // keeps the open flag to tell open from closed roots
         P[j] = j | (kRoots ? kOpen : 0u) | (slot << 16);
-        const uint64_t g = global_index(lat, x0, y0, j);
-        T[g] = (LabelT)g;
+        const uint64_t d = (uint64_t)t * R::kOpenCap + slot;
+        b.G[d] = gword(lat, d, x0, y0, j, slot);
       }
     }
     __syncthreads();
@@ -994,14 +1017,13 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
         const uint32_t rowbase = (uint32_t)(ly * kTW);
         const uint4 v4 = *reinterpret_cast<const uint4*>(P + rowbase + lx0);
         const uint32_t v[4] = {v4.x, v4.y, v4.z, v4.w};
-        uint32_t c[4], rt[4];
+        uint32_t c[4];
         // four independent two-step lookups (run start, root), no branches
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const uint32_t x = v[k] & kIdx;  // run start, or the root for a start
           const uint32_t pr = P[x] & kIdx;
           const uint32_t pvr = P[pr];
-          rt[k] = pr;
           if constexpr (kRoots)
             c[k] = (pvr & kOpen) ? ((pvr >> 16) & 0x1FFu) : (kClosed | pr);
           else
@@ -1015,6 +1037,7 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
           for (int k = 0; k < 4; ++k)
             if (lx0 + k < w) b.code[gi + k] = (uint16_t)c[k];
         }
+        // edge sites belong to open clusters: their codes are open slots
         const bool edge_row = (ly == 0 || ly == h - 1);
         const int last = w - 1 - lx0;
         if (edge_row || lane == 0 || (last >= 0 && last < 4)) {
@@ -1022,10 +1045,10 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
           for (int k = 0; k < 4; ++k) {
             const int lx = lx0 + k;
             if (lx < w) {
-              if (lx == w - 1) edge[ly] = (uint16_t)rt[k];
-              if (lx == 0) edge[TH + ly] = (uint16_t)rt[k];
-              if (ly == h - 1) edge[2 * TH + lx] = (uint16_t)rt[k];
-              if (ly == 0) edge[2 * TH + kTW + lx] = (uint16_t)rt[k];
+              if (lx == w - 1) edge[ly] = (uint16_t)c[k];
+              if (lx == 0) edge[TH + ly] = (uint16_t)c[k];
+              if (ly == h - 1) edge[2 * TH + lx] = (uint16_t)c[k];
+              if (ly == 0) edge[2 * TH + kTW + lx] = (uint16_t)c[k];
             }
           }
         }
@@ -1067,7 +1090,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__
   const uint64_t item = (uint64_t)blockIdx.x * kMergeThreads + threadIdx.x;
   const uint32_t g = (uint32_t)(item / kPer);
   const int pos = (int)(item % kPer);
-  LabelT a = (LabelT)~(LabelT)0, c = (LabelT)~(LabelT)0;
+  uint64_t a = 0, c = 0;  // the two nodes of an active crossing bond
+  uint32_t key = 0xFFFFFFFFu;  // (parity of g, edge, slot of a, slot of c): unique within a warp
   bool active = false;
   const uint32_t rep = g < src.ntiles() ? src.rep(g) : 0u;
   const Bufs& b = src.bufs(rep);
@@ -1085,31 +1109,32 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__
       const int ly = pos;
       if (ly < h && ((bits[ly >> 5] >> (ly & 31)) & 1u)) {
         const uint32_t tn = ty * lat.ntx + (tx + 1 == lat.ntx ? 0u : tx + 1);
-        uint64_t nx0, ny0;
-        int nw, nh;
-        tile_geom(lat, tn, TH, nx0, ny0, nw, nh);
-        a = (LabelT)global_index(lat, x0, y0, edge[ly]);
-        c = (LabelT)global_index(lat, nx0, ny0, b.edge[(uint64_t)tn * R::kEdge + TH + ly]);
+        const uint32_t sa = edge[ly], sc = b.edge[(uint64_t)tn * R::kEdge + TH + ly];
+        a = (uint64_t)t * R::kOpenCap + sa;
+        c = (uint64_t)tn * R::kOpenCap + sc;
+        key = ((g & 1u) << 19) | (sa << kSlotBits) | sc;
         active = true;
       }
     } else {
       const int lx = pos - TH;
       if (lx < w && ((bits[R::kRightWords + (lx >> 5)] >> (lx & 31)) & 1u)) {
         const uint32_t tn = (ty + 1 == lat.nty ? 0u : ty + 1) * lat.ntx + tx;
-        uint64_t nx0, ny0;
-        int nw, nh;
-        tile_geom(lat, tn, TH, nx0, ny0, nw, nh);
-        a = (LabelT)global_index(lat, x0, y0, edge[2 * TH + lx]);
-        c = (LabelT)global_index(lat, nx0, ny0, b.edge[(uint64_t)tn * R::kEdge + 2 * TH + kTW + lx]);
+        const uint32_t sa = edge[2 * TH + lx], sc = b.edge[(uint64_t)tn * R::kEdge + 2 * TH + kTW + lx];
+        a = (uint64_t)t * R::kOpenCap + sa;
+        c = (uint64_t)tn * R::kOpenCap + sc;
+        key = ((g & 1u) << 19) | (1u << 18) | (sa << kSlotBits) | sc;
         active = true;
       }
     }
   }
   // neighbouring edge sites usually repeat the same pair of roots: one lane
-  // per distinct (a, c) pair does the union
-  const unsigned same = __match_any_sync(0xFFFFFFFFu, a) & __match_any_sync(0xFFFFFFFFu, c);
+  // per distinct (a, c) pair does the union.  A warp's positions lie in at
+  // most two consecutive global tiles g (TH + 128 >= 32 positions each), so
+  // g's parity, the edge (right or bottom) and the two open slots name the
+  // pair.
+  const unsigned same = __match_any_sync(0xFFFFFFFFu, key);
   if (active && (int)(threadIdx.x & 31) == __ffs(same) - 1)
-    unite_global(reinterpret_cast<LabelT*>(b.T), a, c, b.err, b.walk_cap ? b.walk_cap : kFindCap);
+    gunite<TH>(b.G, lat, a, c, b.err, b.walk_cap ? b.walk_cap : kFindCap);
 
   if (g < src.ntiles() && t == 0 && pos == 0) {
     const unsigned long long s = b.ctl[0];
@@ -1129,31 +1154,33 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__
 }
 
 // ================================================================== k_resolve
-// One warp per tile, a lane per open root: find (and compress to) the global
-// root, draw the cluster's new state once per open root (Sec. 2 step (3)).
+// Sec. 2 step (3) for open clusters: a thread per open root finds (and
+// compresses to) its global root and draws the cluster's new state, keyed
+// by the root's site index.  A tile's open slots are covered by
+// kResolvePer blocks (a thread per slot, the slots past the tile's count
+// leave at once), so every walk of the lattice is in flight together; the
+// tile's nodes are contiguous, so a warp's first loads share sectors.
+constexpr int kResolveThreads = 256;
+
+template <int TH>
+struct ResolveGrid {
+  static constexpr int kPer = (TileRec<TH>::kOpenCap + kResolveThreads - 1) / kResolveThreads;
+};
+
 template <int TH, typename LabelT, typename Src>
-__global__ void __launch_bounds__(kMergeThreads) k_resolve(const __grid_constant__ Src src) {
+__global__ void __launch_bounds__(kResolveThreads) k_resolve(const __grid_constant__ Src src) {
   using R = TileRec<TH>;
-  const uint64_t g = ((uint64_t)blockIdx.x * kMergeThreads + threadIdx.x) >> 5;
-  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t g = blockIdx.x / ResolveGrid<TH>::kPer;
+  const uint32_t k = (blockIdx.x % ResolveGrid<TH>::kPer) * kResolveThreads + threadIdx.x;
   if (g >= src.ntiles()) return;
-  const uint32_t rep = src.rep((uint32_t)g);
+  const uint32_t rep = src.rep(g);
   const Bufs& b = src.bufs(rep);
+  const uint32_t t = g - src.tile0(rep);
+  if (k >= min(b.ocnt[t], (uint32_t)R::kOpenCap)) return;
   const Lattice& lat = src.lattice(rep);
-  const uint32_t t = (uint32_t)g - src.tile0(rep);
-  const uint32_t n = b.ocnt[t];
-  if (lane >= n) return;
-  uint64_t x0, y0;
-  int w, h;
-  tile_geom(lat, t, TH, x0, y0, w, h);
-  LabelT* T = reinterpret_cast<LabelT*>(b.T);
-  const uint32_t sweep = (uint32_t)b.ctl[1];
-  for (uint32_t k = lane; k < n; k += 32) {
-    const uint32_t l = b.olist[(uint64_t)t * R::kOpenCap + k];
-    const LabelT r = find_global(T, (LabelT)global_index(lat, x0, y0, l), b.err, b.walk_cap ? b.walk_cap : kFindCap);
-    b.nso[(uint64_t)t * R::kOpenCap + k] =
-        (uint8_t)pick_state(stream4_rk(b.rk, (uint64_t)r, sweep, kDomSpin).x, b.q);
-  }
+  const uint64_t d = (uint64_t)t * R::kOpenCap + k;
+  const uint64_t r = gfind<TH>(b.G, lat, d, ldcg(b.G + d), b.err, b.walk_cap ? b.walk_cap : kFindCap);
+  b.nso[d] = (uint8_t)pick_state(stream4_rk(b.rk, gsite(lat, r), (uint32_t)b.ctl[1], kDomSpin).x, b.q);
 }
 
 // ================================================================== k_recolor
@@ -1176,9 +1203,7 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const __grid_constant__ Sr
   int w, h;
   tile_geom(lat, t, TH, x0, y0, w, h);
   const uint64_t L = lat.L;
-  LabelT* T = reinterpret_cast<LabelT*>(b.T);
   const uint8_t* nso = b.nso + (uint64_t)t * R::kOpenCap;
-  const uint16_t* ol = b.olist + (uint64_t)t * R::kOpenCap;
   uint32_t jx = 0, Mx = 0;
   if constexpr (kXY) {
     jx = (uint32_t)b.ctl[2];  // the sweep's embedding axis, filed by k_merge
@@ -1246,8 +1271,9 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const __grid_constant__ Sr
             if (c[k] & kClosed) {
               roots[gi + k] = (LabelT)global_index(lat, x0, y0, c[k] & kIdx);
             } else {
-              const uint64_t g = global_index(lat, x0, y0, ol[c[k]]);
-              roots[gi + k] = find_global(T, (LabelT)g, b.err, b.walk_cap ? b.walk_cap : kFindCap);
+              const uint64_t d = (uint64_t)t * R::kOpenCap + c[k];
+              const uint64_t r = gfind<TH>(b.G, lat, d, ldcg(b.G + d), b.err, b.walk_cap ? b.walk_cap : kFindCap);
+              roots[gi + k] = (LabelT)gsite(lat, r);
             }
           }
         }

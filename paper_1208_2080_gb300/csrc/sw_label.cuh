@@ -3,9 +3,10 @@
 //
 // It computes what k_label_tile computes (Sec. 2 steps (1)-(3), tile-local
 // part, plus the measurement of Sec. 4) and writes the same records -- the
-// 16-bit site codes, the four edge lines, the cross-edge bond bits, the
-// open-root list and the initial global labels -- so that k_merge, k_resolve
-// and k_recolor run unchanged after it.  What differs is the work mapping:
+// 16-bit site codes, the open slots of the four edge lines, the cross-edge
+// bond bits and the open roots' nodes of the global union-find -- so that
+// k_merge, k_resolve and k_recolor run unchanged after it.  What differs is
+// the work mapping:
 //
 //   * a lane owns 64 consecutive sites of one tile row (two 32-bit words),
 //     so a warp covers 16 rows of a 128-wide tile and a CTA of TH/16 warps
@@ -30,7 +31,7 @@
 //   C  clusters that touch the tile edge are flagged open at their root;
 //   D  run starts are compressed to their root; a closed cluster draws its
 //      new state at its root (Sec. 2 step (3)), an open root takes a slot in
-//      the tile's open list and a global label;
+//      the tile's open list and its node of the global union-find;
 //   F  per-site codes (16 sites' worth of lanes per row, coalesced 16-byte
 //      stores) and the edge lines.
 //
@@ -320,7 +321,6 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
     const uint32_t q_states = b.q;
     const bool measure = !kGiven && b.measure;
     const uint32_t sweep = kGiven ? 0u : (uint32_t)b.ctl[0];
-    LabelT* T = reinterpret_cast<LabelT*>(b.T);
     uint64_t x0, y0;
     int w, h;
     tile_geom(lat, t, TH, x0, y0, w, h);
@@ -790,9 +790,9 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
     // (NR).  The lanes queue their roots and take them in lockstep: a
     // closed root draws its cluster's new state (Sec. 2 step (3)), an open
     // root (flagged in phase C) takes a slot in the tile's open list (in
-    // whatever order: a slot only names the root to later kernels) and a
-    // global label.  Other starts keep pointing at their root: phase F
-    // looks the code up there.
+    // whatever order: a slot only names the root to later kernels) and its
+    // node of the global union-find.  Other starts keep pointing at their
+    // root: phase F looks the code up there.
     {
       volatile uint16_t* vp = P;
       uint64_t rem = 0;
@@ -810,9 +810,8 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
           if (k < nq) {
             if (e & kMarkA) {
               const uint32_t slot = atomicAdd(&wcnt[0], 1u);
-              b.olist[(uint64_t)t * R::kOpenCap + slot] = (uint16_t)r;
-              const uint64_t gr = global_index(lat, x0, y0, r);
-              T[gr] = (LabelT)gr;
+              const uint64_t d = (uint64_t)t * R::kOpenCap + slot;
+              b.G[d] = gword(lat, d, x0, y0, r, slot);
               vp[r] = (uint16_t)(kMarkB | slot);
             } else {
               uint32_t code;
@@ -919,19 +918,20 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
             for (int k = 0; k < 8; ++k)
               if (cx + k < w) b.code[gi + k] = (uint16_t)cd[k];
           }
+          // edge sites belong to open clusters: their codes are open slots
           if (yy == 0 || yy == h - 1) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
               if (cx + k < w) {
-                if (yy == h - 1) edge[2 * TH + cx + k] = (uint16_t)rt[k];
-                if (yy == 0) edge[2 * TH + kTW + cx + k] = (uint16_t)rt[k];
+                if (yy == h - 1) edge[2 * TH + cx + k] = (uint16_t)cd[k];
+                if (yy == 0) edge[2 * TH + kTW + cx + k] = (uint16_t)cd[k];
               }
             }
           }
-          if (cx == 0) edge[TH + yy] = (uint16_t)rt[0];
+          if (cx == 0) edge[TH + yy] = (uint16_t)cd[0];
 #pragma unroll
           for (int k = 0; k < 8; ++k)
-            if (cx + k == w - 1) edge[yy] = (uint16_t)rt[k];
+            if (cx + k == w - 1) edge[yy] = (uint16_t)cd[k];
         }
       }
       if (tid == 0) b.ocnt[t] = wcnt[0];

@@ -116,9 +116,9 @@ cudaError_t launch_merge_src(const Src& src, uint32_t ntiles, cudaStream_t st) {
 
 template <int TH, typename LabelT, typename Src>
 cudaError_t launch_resolve_src(const Src& src, uint32_t ntiles, cudaStream_t st) {
-  const uint64_t items = (uint64_t)ntiles * 32;  // a warp per tile
-  const uint64_t blocks = (items + kMergeThreads - 1) / kMergeThreads;
-  k_resolve<TH, LabelT, Src><<<(unsigned)blocks, kMergeThreads, 0, st>>>(src);
+  const uint64_t blocks = (uint64_t)ntiles * ResolveGrid<TH>::kPer;
+  if (blocks == 0) return cudaSuccess;
+  k_resolve<TH, LabelT, Src><<<(unsigned)blocks, kResolveThreads, 0, st>>>(src);
   return cudaGetLastError();
 }
 

@@ -21,8 +21,9 @@ namespace {
 
 // Working memory of every call, on every device that loads the library,
 // held until the process exits.  Sized for L <= SW_LABEL_STATIC_MAX_L with
-// any tile height: per-site codes (2 B/site) and labels (4 B/site) plus the
-// per-tile edge records and control words.
+// any tile height: per-site codes (2 B/site), the global union-find (8 B
+// per possible open root of a tile), the per-tile edge records and control
+// words (under 4 MiB at L = 1024 with the smallest tiles).
 constexpr size_t kScratchBytes = 8u << 20;
 static __device__ __align__(256) unsigned char g_label_scratch[kScratchBytes];
 
@@ -86,11 +87,10 @@ extern "C" int sw_label_bonds_static(uint64_t L, const uint8_t* bonds, uint32_t*
 
   // layout of the working memory
   const size_t o_code = 0;
-  const size_t o_T = o_code + up256(2 * N + 16);
-  const size_t o_edge = o_T + up256(4 * N);
+  const size_t o_G = o_code + up256(2 * N + 16);
+  const size_t o_edge = o_G + up256(nt * open_cap(th) * 8);
   const size_t o_ebits = o_edge + up256(nt * edge_u16(th) * 2);
-  const size_t o_olist = o_ebits + up256(nt * bit_words(th) * 4);
-  const size_t o_ocnt = o_olist + up256(nt * open_cap(th) * 2);
+  const size_t o_ocnt = o_ebits + up256(nt * bit_words(th) * 4);
   const size_t o_ctl = o_ocnt + up256(nt * 4);
   const size_t o_err = o_ctl + 256;
   if (o_err + 256 > kScratchBytes) return SW_ERR_INVAL;
@@ -102,10 +102,9 @@ extern "C" int sw_label_bonds_static(uint64_t L, const uint8_t* bonds, uint32_t*
   Bufs b{};
   b.bonds = const_cast<uint8_t*>(bonds);
   b.code = reinterpret_cast<uint16_t*>(base + o_code);
-  b.T = base + o_T;
+  b.G = reinterpret_cast<uint64_t*>(base + o_G);
   b.edge = reinterpret_cast<uint16_t*>(base + o_edge);
   b.ebits = reinterpret_cast<uint32_t*>(base + o_ebits);
-  b.olist = reinterpret_cast<uint16_t*>(base + o_olist);
   b.ocnt = reinterpret_cast<uint32_t*>(base + o_ocnt);
   b.ctl = reinterpret_cast<unsigned long long*>(base + o_ctl);
   b.err = reinterpret_cast<uint32_t*>(base + o_err);
@@ -116,7 +115,6 @@ extern "C" int sw_label_bonds_static(uint64_t L, const uint8_t* bonds, uint32_t*
   // the array keeps the previous call's contents: clear what must start at zero
   cudaError_t e = cudaMemsetAsync(b.ctl, 0, 256, st);
   if (!e) e = cudaMemsetAsync(b.err, 0, 256, st);
-  if (!e) e = cudaMemsetAsync(b.T, 0, 4 * N, st);
   if (!e) {
     switch (th) {
       case 16: e = label_static<16>(b, lat, roots, st); break;

@@ -456,21 +456,20 @@ int wolff_label_setup(sw_wolff* w) {
   w->a.roots = (uint32_t*)wtake(w, w->N * 4);
   b.bonds = w->a.bonds;
   b.code = (uint16_t*)wtake(w, w->N * 2 + 16);
-  b.T = wtake(w, w->N * 4);
+  b.G = (uint64_t*)wtake(w, nt * open_cap(th) * 8);
   b.edge = (uint16_t*)wtake(w, nt * edge_u16(th) * 2);
   b.ebits = (uint32_t*)wtake(w, nt * bit_words(th) * 4);
-  b.olist = (uint16_t*)wtake(w, nt * open_cap(th) * 2);
   b.ocnt = (uint32_t*)wtake(w, nt * 4);
   b.ctl = (unsigned long long*)wtake(w, 64);
   b.err = (uint32_t*)wtake(w, 64);
   b.q = 2;
   b.measure = 0;
-  if (!w->a.bonds || !w->a.roots || !b.code || !b.T || !b.edge || !b.ebits || !b.olist || !b.ocnt ||
+  if (!w->a.bonds || !w->a.roots || !b.code || !b.G || !b.edge || !b.ebits || !b.ocnt ||
       !b.ctl || !b.err) {
     w->a.roots = nullptr;  // the blocks taken so far are freed with the handle
     return SW_ERR_NOMEM;
   }
-  cudaError_t e = cudaMemsetAsync(b.T, 0, w->N * 4, w->stream);
+  cudaError_t e = cudaMemsetAsync(b.G, 0, nt * open_cap(th) * 8, w->stream);
   if (!e) e = cudaMemsetAsync(b.ctl, 0, 64, w->stream);
   if (!e) e = cudaMemsetAsync(b.err, 0, 64, w->stream);
   if (!e) e = cudaMemsetAsync(b.ocnt, 0, nt * 4, w->stream);

@@ -296,10 +296,9 @@ int sw_xy_create(const sw_xy_params* prm, sw_xy** out) {
   b.spin = (uint8_t*)xtake(s, s->N + 16);
   b.code = (uint16_t*)xtake(s, s->N * 2 + 16);
   b.bonds = nullptr;
-  b.T = xtake(s, s->N * (lb / 8));
+  b.G = (uint64_t*)xtake(s, nt * open_cap(th) * 8);
   b.edge = (uint16_t*)xtake(s, nt * edge_u16(th) * 2);
   b.ebits = (uint32_t*)xtake(s, nt * bit_words(th) * 4);
-  b.olist = (uint16_t*)xtake(s, nt * open_cap(th) * 2);
   b.ocnt = (uint32_t*)xtake(s, nt * 4);
   b.nso = (uint8_t*)xtake(s, nt * open_cap(th));
   b.acc = (unsigned long long*)xtake(s, 8 * kMaxAcc);
@@ -307,7 +306,7 @@ int sw_xy_create(const sw_xy_params* prm, sw_xy** out) {
   b.ctl = (unsigned long long*)xtake(s, 64);
   b.err = (uint32_t*)xtake(s, 64);
   uint32_t* tt = (uint32_t*)xtake(s, ntri * 4);
-  if (!b.spin || !b.code || !b.T || !b.edge || !b.ebits || !b.olist || !b.ocnt || !b.nso || !b.acc ||
+  if (!b.spin || !b.code || !b.G || !b.edge || !b.ebits || !b.ocnt || !b.nso || !b.acc ||
       !b.ring || !b.ctl || !b.err || !tt) {
     xrelease(s);
     delete s;
@@ -328,7 +327,7 @@ int sw_xy_create(const sw_xy_params* prm, sw_xy** out) {
     for (uint32_t d = 0; d <= c; ++d) host_tri[c * (c + 1) / 2 + d] = host_tt[c * (s->H + 1) + d];
   cudaError_t e = cudaMemcpyAsync(tt, host_tri.data(), ntri * 4, cudaMemcpyHostToDevice, s->stream);
   if (!e) e = cudaStreamSynchronize(s->stream);  // host_tri is a stack-lifetime buffer
-  if (!e) e = cudaMemsetAsync(b.T, 0, s->N * (lb / 8), s->stream);
+  if (!e) e = cudaMemsetAsync(b.G, 0, nt * open_cap(th) * 8, s->stream);
   if (!e) e = cudaMemsetAsync(b.acc, 0, 8 * kMaxAcc, s->stream);
   if (!e) e = cudaMemsetAsync(b.ring, 0xFF, (size_t)s->ring * rec * 8, s->stream);
   if (!e) e = cudaMemsetAsync(b.ctl, 0, 64, s->stream);
