@@ -266,7 +266,13 @@ def run_ours(args, rank, world):
     N = L * L
     T = sw.tc(q)
     seed = 5 + rank
-    sim = sw.Sim(L, q, T, seed, init="zero", label_bits=args.label_bits, tile_h=args.tile_h)
+    sim = sw.Sim(L, q, T, seed, init="zero", label_bits=args.label_bits, tile_h=args.tile_h,
+                 merge=args.merge)
+    if sim.info()["merge"] == sw._binding.MERGE["fused"]:
+        # the labeller does the boundary unions; a one-block filing kernel
+        # takes k_merge's place in the launch sequence
+        ALG_BYTES_PER_SITE["k_file+k_resolve"] = ALG_BYTES_PER_SITE.pop("k_merge+k_resolve")
+        PHASES[1] = "k_file+k_resolve"
     info = sim.info()
     stream = torch.cuda.current_stream()
     evw0, evw1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -315,7 +321,7 @@ def run_ours(args, rank, world):
         sim = None
         torch.cuda.empty_cache()
         sim2 = sw.Sim(L, q, T, seed, measure=False, label_bits=args.label_bits,
-                      tile_h=args.tile_h)
+                      tile_h=args.tile_h, merge=args.merge)
         sim2.set_spins(spins_dev)
         sim2.set_sweep(cur)
         del spins_dev
@@ -426,6 +432,7 @@ def run_ours(args, rank, world):
                                f"uint{info['label_bits']} labels, sweeps {args.warmup}.."
                                f"{args.warmup + args.steps - 1}",
                    "L": L, "q": q, "tile": f"{info['tile_w']}x{info['tile_h']}",
+                   "merge": sw._binding.MERGE_NAMES[info["merge"]],
                    "l2": "inputs larger than L2 (4 GiB spins, 8 GiB codes at L=65536)",
                    "replicas": world},
         "gpu_launches": LAUNCHES_PER_SWEEP * args.steps,
@@ -540,7 +547,8 @@ def run_wolff(args, sw, torch):
 def run_batched(args, sw, torch):
     """Replica sweeps/s of the 512-replica batch (L = 64..2048 log-uniform,
     q in {2,3,4,5,8}, T in [0.9, 1.1] T_c(q), one Philox key each): all
-    replicas in one batch (autotuned tile height / launch mode) against the
+    replicas in one batch (autotuned tile height / merge schedule / launch
+    mode) against the
     same replicas swept one at a time through the single-lattice API."""
     import numpy as np
 
@@ -551,7 +559,8 @@ def run_batched(args, sw, torch):
     cfg = tune.tune_batch(p["L"], p["q"], p["T"], p["seed"])
     stream = torch.cuda.current_stream()
     out = {"R": R, "sites": int((p["L"].astype(np.float64) ** 2).sum()), "tuned": cfg}
-    with sw.Batch(p["L"], p["q"], p["T"], p["seed"], tile_h=cfg["tile_h"], graph=cfg["graph"]) as b:
+    with sw.Batch(p["L"], p["q"], p["T"], p["seed"], tile_h=cfg["tile_h"], graph=cfg["graph"],
+                  merge=cfg.get("merge", "kernel")) as b:
         b.sweep(3)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -596,6 +605,8 @@ def main():
     ap.add_argument("--L", type=int, default=65536, help="lattice size (default: the workload)")
     ap.add_argument("--label-bits", type=int, default=0, help="0 = auto (64 above L=32768)")
     ap.add_argument("--tile-h", type=int, default=0, help="labelling tile height (0 = auto)")
+    ap.add_argument("--merge", default="auto", choices=["auto", "kernel", "fused"],
+                    help="boundary-union schedule")
     ap.add_argument("--ref-L", type=int, default=4096, help="oracle sample size per reference step")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--update-only-steps", type=int, default=20)

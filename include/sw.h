@@ -76,6 +76,17 @@ typedef struct {
   uint64_t n[256]; /* sites in each state */
 } sw_obs;
 
+/* Boundary-union schedules (Sec. 2 step (2), global part; Sec. 3's
+ * boundary-only stage on one GPU): SW_MERGE_KERNEL unites the clusters
+ * across tile edges in a kernel of its own after the labelling;
+ * SW_MERGE_FUSED has the labelling do it: of the two tiles that share an
+ * edge, the one that finishes second unites across it (an atomic counter
+ * per edge decides, nothing waits).  Same results; the batch autotuner
+ * times both. */
+#define SW_MERGE_AUTO 0u
+#define SW_MERGE_KERNEL 1u
+#define SW_MERGE_FUSED 2u
+
 /* Creation parameters; zero means "default" for every optional field. */
 typedef struct {
   uint64_t L;           /* linear size, >= 2 (N = L*L sites) */
@@ -105,7 +116,10 @@ typedef struct {
                            runs into it reports SW_ERR_TIMEOUT (sw_sync,
                            sw_measure) and the handle refuses further work.
                            A small value is for tests of that path. */
-  uint32_t reserved[2];
+  uint32_t merge;       /* boundary-union schedule, SW_MERGE_*: 0 = auto
+                           (SW_MERGE_KERNEL, the faster one for a single
+                           lattice on GB300), results do not depend on it */
+  uint32_t reserved[1];
 } sw_params;
 
 /* Library-wide device allocator (e.g. a framework's caching allocator).
@@ -195,6 +209,8 @@ typedef struct {
   uint32_t ring;
   uint64_t device_bytes; /* device memory held by the handle */
   uint64_t tiles;
+  uint32_t merge;        /* SW_MERGE_KERNEL or SW_MERGE_FUSED */
+  uint32_t pad_;
 } sw_info_t;
 int sw_info(const sw_sim *sim, sw_info_t *out);
 
@@ -241,7 +257,9 @@ typedef struct {
   uint32_t init;        /* SW_INIT_RANDOM or SW_INIT_ZERO */
   uint32_t measure;     /* 0 = on, 2 = off */
   uint32_t graph;       /* 0 = replay sweeps as a CUDA graph, 2 = plain launches */
-  uint32_t reserved[4];
+  uint32_t merge;       /* boundary-union schedule, SW_MERGE_* (0 = auto:
+                           SW_MERGE_KERNEL) */
+  uint32_t reserved[3];
 } sw_batch_params;
 
 typedef struct {
@@ -252,6 +270,8 @@ typedef struct {
   uint64_t device_bytes; /* device memory held (one arena) */
   uint32_t label_bits;   /* 32, or 64 if any L > 32768 */
   uint32_t graph;        /* 1 if sweeps replay a CUDA graph */
+  uint32_t merge;        /* SW_MERGE_KERNEL or SW_MERGE_FUSED */
+  uint32_t pad_;
 } sw_batch_info_t;
 
 /* Create R replicas (host arrays are read during the call only); one device

@@ -58,12 +58,19 @@ class sw_obs(ctypes.Structure):
                 ("pad_", ctypes.c_uint32), ("n", ctypes.c_uint64 * 256)]
 
 
+# boundary-union schedules (include/sw.h SW_MERGE_*): "kernel" -- a kernel
+# of its own after the labelling; "fused" -- the labelling does it
+MERGE = {"auto": 0, "kernel": 1, "fused": 2}
+MERGE_NAMES = {1: "kernel", 2: "fused"}
+
+
 class sw_params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_uint64), ("q", ctypes.c_uint32), ("label_bits", ctypes.c_uint32),
                 ("T", ctypes.c_double), ("seed", ctypes.c_uint64), ("tile_h", ctypes.c_uint32),
                 ("ring", ctypes.c_uint32), ("init", ctypes.c_uint32),
                 ("store_bonds", ctypes.c_uint32), ("measure", ctypes.c_uint32),
-                ("walk_cap", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
+                ("walk_cap", ctypes.c_uint32), ("merge", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 1)]
 
 
 class sw_xy_params(ctypes.Structure):
@@ -77,7 +84,8 @@ class sw_info_t(ctypes.Structure):
     _fields_ = [("L", ctypes.c_uint64), ("q", ctypes.c_uint32), ("thr", ctypes.c_uint32),
                 ("label_bits", ctypes.c_uint32), ("tile_w", ctypes.c_uint32),
                 ("tile_h", ctypes.c_uint32), ("ring", ctypes.c_uint32),
-                ("device_bytes", ctypes.c_uint64), ("tiles", ctypes.c_uint64)]
+                ("device_bytes", ctypes.c_uint64), ("tiles", ctypes.c_uint64),
+                ("merge", ctypes.c_uint32), ("pad_", ctypes.c_uint32)]
 
 
 class sw_batch_params(ctypes.Structure):
@@ -85,13 +93,15 @@ class sw_batch_params(ctypes.Structure):
                 ("L", ctypes.POINTER(ctypes.c_uint64)), ("q", ctypes.POINTER(ctypes.c_uint32)),
                 ("T", ctypes.POINTER(ctypes.c_double)), ("seed", ctypes.POINTER(ctypes.c_uint64)),
                 ("ring", ctypes.c_uint32), ("init", ctypes.c_uint32), ("measure", ctypes.c_uint32),
-                ("graph", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 4)]
+                ("graph", ctypes.c_uint32), ("merge", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 3)]
 
 
 class sw_batch_info_t(ctypes.Structure):
     _fields_ = [("R", ctypes.c_uint32), ("tile_h", ctypes.c_uint32), ("tiles", ctypes.c_uint64),
                 ("sites", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
-                ("label_bits", ctypes.c_uint32), ("graph", ctypes.c_uint32)]
+                ("label_bits", ctypes.c_uint32), ("graph", ctypes.c_uint32),
+                ("merge", ctypes.c_uint32), ("pad_", ctypes.c_uint32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -258,7 +268,7 @@ class Sim:
     """One L x L lattice on the GPU (include/sw.h handle)."""
 
     def __init__(self, L, q, T, seed, *, label_bits=0, tile_h=0, ring=0, init="random",
-                 store_bonds=False, measure=True, walk_cap=0, stream=None):
+                 store_bonds=False, measure=True, walk_cap=0, merge="auto", stream=None):
         if not _allocator_chosen:
             use_torch_allocator()
         p = sw_params()
@@ -268,6 +278,7 @@ class Sim:
         p.store_bonds = 1 if store_bonds else 0
         p.measure = 0 if measure else 2
         p.walk_cap = int(walk_cap)
+        p.merge = MERGE[merge]
         h = ctypes.c_void_p()
         self._h = None
         check(lib().sw_create_ex(ctypes.byref(p), ctypes.byref(h)), "sw_create_ex")
@@ -581,7 +592,7 @@ class Batch:
     """R independent replicas swept together (include/sw.h, sw_batch_*)."""
 
     def __init__(self, L, q, T, seed, *, tile_h=0, ring=0, init="random", measure=True,
-                 graph=True, stream=None):
+                 graph=True, merge="auto", stream=None):
         if not _allocator_chosen:
             use_torch_allocator()
         self.L = np.ascontiguousarray(np.asarray(L, dtype=np.uint64))
@@ -598,6 +609,7 @@ class Batch:
         p.init = SW_INIT_ZERO if init == "zero" else SW_INIT_RANDOM
         p.measure = 0 if measure else 2
         p.graph = 0 if graph else 2
+        p.merge = MERGE[merge]
         h = ctypes.c_void_p()
         self._h = None
         check(lib().sw_batch_create_ex(ctypes.byref(p), ctypes.byref(h)), "sw_batch_create_ex")

@@ -104,8 +104,8 @@ static cudaError_t launch_recolor_t(const Bufs& b, const Lattice& lat, LabelT* r
 cudaError_t launch_sweep_events(uint32_t label_bits, uint32_t th, const Bufs& b, const Lattice& lat,
                                 cudaStream_t st, cudaEvent_t* ev) {
   const SingleSrc src{b, lat};
-  return label_bits == 64 ? sweep_th<uint64_t>(th, src, lat.ntiles, st, ev)
-                          : sweep_th<uint32_t>(th, src, lat.ntiles, st, ev);
+  return label_bits == 64 ? sweep_th<uint64_t>(th, src, lat.ntiles, st, ev, 1, b.fuse != 0)
+                          : sweep_th<uint32_t>(th, src, lat.ntiles, st, ev, 1, b.fuse != 0);
 }
 
 cudaError_t launch_sweep(uint32_t label_bits, uint32_t th, const Bufs& b, const Lattice& lat,
@@ -323,7 +323,11 @@ cudaError_t sweep_banded(sw_sim* s, const uint32_t* r, uint32_t nb) {
       return e;
   }
   const SingleSrc full{s->b, lat};
-  if ((e = launch_merge_src<TH, LabelT>(full, lat.ntiles, s->stream))) return e;
+  if (s->b.fuse) {
+    if ((e = launch_file_src(full, 1, s->stream))) return e;
+  } else {
+    if ((e = launch_merge_src<TH, LabelT>(full, lat.ntiles, s->stream))) return e;
+  }
   if ((e = launch_resolve_src<TH, LabelT>(full, lat.ntiles, s->stream))) return e;
   return launch_recolor_src<TH, LabelT, false>(full, lat.ntiles, (LabelT*)nullptr, s->stream);
 }
@@ -372,7 +376,8 @@ int sw_create_ex(const sw_params* prm, sw_sim** out) {
   *out = nullptr;
   const uint64_t L = prm->L;
   if (L < 2 || L > (1ull << 20) || prm->q < 2 || prm->q > 255 || !(prm->T > 0.0) ||
-      !isfinite(prm->T) || prm->init > SW_INIT_ZERO || prm->store_bonds > 1 || prm->measure > 2)
+      !isfinite(prm->T) || prm->init > SW_INIT_ZERO || prm->store_bonds > 1 || prm->measure > 2 ||
+      prm->merge > SW_MERGE_FUSED)
     return SW_ERR_INVAL;
   uint32_t lb = prm->label_bits ? prm->label_bits : (L <= 32768 ? 32u : 64u);
   if (lb != 32 && lb != 64) return SW_ERR_INVAL;
@@ -406,12 +411,14 @@ int sw_create_ex(const sw_params* prm, sw_sim** out) {
   b.ebits = (uint32_t*)take(s, nt * bit_words(th) * 4);
   b.ocnt = (uint32_t*)take(s, nt * 4);
   b.nso = (uint8_t*)take(s, nt * open_cap(th));
+  b.fuse = prm->merge == SW_MERGE_FUSED ? 1u : 0u;
+  b.ecnt = b.fuse ? (uint32_t*)take(s, nt * 2 * 4) : nullptr;
   b.acc = (unsigned long long*)take(s, 8 * 260);
   b.ring = (unsigned long long*)take(s, (size_t)ring * (2 + s->q) * 8);
   b.ctl = (unsigned long long*)take(s, 64);
   b.err = (uint32_t*)take(s, 64);
   if (!b.spin || !b.code || (prm->store_bonds && !b.bonds) || !b.G || !b.edge || !b.ebits ||
-      !b.ocnt || !b.nso || !b.acc || !b.ring || !b.ctl || !b.err) {
+      !b.ocnt || !b.nso || (b.fuse && !b.ecnt) || !b.acc || !b.ring || !b.ctl || !b.err) {
     release_all(s);
     delete s;
     return SW_ERR_NOMEM;
@@ -431,6 +438,7 @@ int sw_create_ex(const sw_params* prm, sw_sim** out) {
   if (!e) e = cudaMemsetAsync(b.ctl, 0, 64, s->stream);
   if (!e) e = cudaMemsetAsync(b.err, 0, 64, s->stream);
   if (!e) e = cudaMemsetAsync(b.ocnt, 0, nt * 4, s->stream);
+  if (!e && b.fuse) e = cudaMemsetAsync(b.ecnt, 0, nt * 2 * 4, s->stream);  // every counter even
   if (!e) e = launch_init(b.spin, s->N, s->q, prm->seed, prm->init, s->stream);
   if (!e) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) {
@@ -749,6 +757,8 @@ int sw_info(const sw_sim* s, sw_info_t* out) {
   out->ring = s->ring;
   out->device_bytes = s->dev_bytes;
   out->tiles = s->lat.ntiles;
+  out->merge = s->b.fuse ? SW_MERGE_FUSED : SW_MERGE_KERNEL;
+  out->pad_ = 0;
   return SW_OK;
 }
 

@@ -20,6 +20,7 @@ using namespace swgb;
 struct sw_batch {
   uint32_t R = 0, th = 64, ring = 64, label_bits = 32;
   bool measure_on = true, want_graph = true;
+  bool fuse = false;  // the labeller does the boundary unions (SW_MERGE_FUSED)
   DeviceAllocator alloc{};
   void* arena = nullptr;
   size_t arena_bytes = 0;
@@ -84,8 +85,8 @@ int check_err(sw_batch* b) {
 
 cudaError_t batch_sweep_once(sw_batch* b, cudaStream_t st, cudaEvent_t* ev) {
   const BatchSrc src{b->d_reps, b->d_tile_rep, b->total, b->R};
-  return b->label_bits == 64 ? sweep_th<uint64_t>(b->th, src, b->total, st, ev)
-                             : sweep_th<uint32_t>(b->th, src, b->total, st, ev);
+  return b->label_bits == 64 ? sweep_th<uint64_t>(b->th, src, b->total, st, ev, b->R, b->fuse)
+                             : sweep_th<uint32_t>(b->th, src, b->total, st, ev, b->R, b->fuse);
 }
 
 // Captures one batch sweep into a graph (on a private stream; the graph
@@ -153,7 +154,7 @@ int sw_batch_create_ex(const sw_batch_params* p, sw_batch** out) {
   *out = nullptr;
   const uint32_t th = p->tile_h ? p->tile_h : 64u;
   if (th != 16 && th != 32 && th != 64 && th != 128) return SW_ERR_INVAL;
-  if (p->init > SW_INIT_ZERO || p->measure > 2 || p->graph > 2) return SW_ERR_INVAL;
+  if (p->init > SW_INIT_ZERO || p->measure > 2 || p->graph > 2 || p->merge > SW_MERGE_FUSED) return SW_ERR_INVAL;
   uint32_t lb = 32;
   for (uint32_t r = 0; r < p->R; ++r) {
     if (p->L[r] < 2 || p->L[r] > (1ull << 20) || p->q[r] < 2 || p->q[r] > 255 ||
@@ -169,6 +170,7 @@ int sw_batch_create_ex(const sw_batch_params* p, sw_batch** out) {
   b->label_bits = lb;
   b->measure_on = p->measure != 2;
   b->want_graph = p->graph != 2;
+  b->fuse = p->merge == SW_MERGE_FUSED;
   b->alloc = current_allocator();
   b->reps.resize(p->R);
   b->pending.assign(p->R, 1);
@@ -185,7 +187,7 @@ int sw_batch_create_ex(const sw_batch_params* p, sw_batch** out) {
     off[r] = bytes;
     bytes += up256(N + 16) + up256(2 * N + 16) + up256(nt * open_cap(th) * 8) + up256(nt * edge_u16(th) * 2) +
              up256(nt * bit_words(th) * 4) + up256(nt * 4) +
-             up256(nt * open_cap(th)) + up256(8 * 260) + up256((size_t)b->ring * (2 + p->q[r]) * 8) +
+             up256(nt * open_cap(th)) + up256(nt * 2 * 4) + up256(8 * 260) + up256((size_t)b->ring * (2 + p->q[r]) * 8) +
              up256(64);
     total += nt;
     b->sites += N;
@@ -225,6 +227,8 @@ int sw_batch_create_ex(const sw_batch_params* p, sw_batch** out) {
     bb.ebits = (uint32_t*)c; c += up256(nt * bit_words(th) * 4);
     bb.ocnt = (uint32_t*)c; c += up256(nt * 4);
     bb.nso = c; c += up256(nt * open_cap(th));
+    bb.ecnt = (uint32_t*)c; c += up256(nt * 2 * 4);
+    bb.fuse = b->fuse ? 1u : 0u;
     bb.acc = (unsigned long long*)c; c += up256(8 * 260);
     bb.ring = (unsigned long long*)c; c += up256((size_t)b->ring * (2 + p->q[r]) * 8);
     bb.ctl = (unsigned long long*)c;
@@ -424,6 +428,8 @@ int sw_batch_info(const sw_batch* b, sw_batch_info_t* out) {
   out->device_bytes = b->arena_bytes;
   out->label_bits = b->label_bits;
   out->graph = b->want_graph ? 1u : 0u;
+  out->merge = b->fuse ? SW_MERGE_FUSED : SW_MERGE_KERNEL;
+  out->pad_ = 0;
   return SW_OK;
 }
 

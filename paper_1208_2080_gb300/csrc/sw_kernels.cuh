@@ -133,6 +133,8 @@ struct Bufs {
   uint32_t measure;           // 1: k_label_tile accumulates observables of its input
   uint32_t rk[20];            // Philox round keys of `seed` (see set_round_keys)
   uint32_t walk_cap;          // bound on a global union-find walk (0: kFindCap)
+  uint32_t fuse;              // 1: the labeller unites across tile edges (no k_merge)
+  uint32_t* ecnt;             // fuse: 2 * ntiles edge counters (right, bottom edge of each tile)
   // XY model (embedded clusters, M angles; q = 2 coins): 0 for Potts
   uint32_t M;
   const uint32_t* tt;         // bond thresholds by |sigma| fold indices (c >= d): tt[c(c+1)/2 + d]
@@ -168,6 +170,7 @@ struct SingleSrc {
   static constexpr bool kMulti = false;
   static constexpr bool kCheck = false;
   __device__ __forceinline__ uint32_t ntiles() const { return lat.ntiles; }
+  __device__ __forceinline__ uint32_t nreps() const { return 1; }
   __device__ __forceinline__ uint32_t rep(uint32_t) const { return 0; }
   __device__ __forceinline__ const Bufs& bufs(uint32_t) const { return b; }
   __device__ __forceinline__ const Lattice& lattice(uint32_t) const { return lat; }
@@ -182,6 +185,7 @@ struct BatchSrc {
   static constexpr bool kMulti = true;
   static constexpr bool kCheck = false;
   __device__ __forceinline__ uint32_t ntiles() const { return total; }
+  __device__ __forceinline__ uint32_t nreps() const { return nrep; }
   __device__ __forceinline__ uint32_t rep(uint32_t g) const { return __ldg(tile_rep + g); }
   __device__ __forceinline__ const Bufs& bufs(uint32_t r) const { return reps[r].b; }
   __device__ __forceinline__ const Lattice& lattice(uint32_t r) const { return reps[r].lat; }
@@ -198,6 +202,7 @@ struct BandSrc {
   static constexpr bool kMulti = false;
   static constexpr bool kCheck = true;
   __device__ __forceinline__ uint32_t ntiles() const { return count; }
+  __device__ __forceinline__ uint32_t nreps() const { return 1; }
   __device__ __forceinline__ uint32_t rep(uint32_t) const { return 0; }
   __device__ __forceinline__ const Bufs& bufs(uint32_t) const { return b; }
   __device__ __forceinline__ const Lattice& lattice(uint32_t) const { return lat; }
@@ -1078,14 +1083,64 @@ __global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks
   }
 }
 
+// ================================================================== boundary unions
+// The crossing bond at edge position pos of tile t (0 .. TH-1: row of the
+// right edge, TH .. TH+127: column of the bottom edge; the periodic wrap
+// included): true if it is active, with its two nodes (t's, the
+// neighbour's) and their open slots.  kCG: loads that bypass L1 (records
+// another SM wrote during this launch).  The bond bit and both slots are
+// loaded together; the slots of a position without an active bond are not
+// used.
+template <int TH, bool kCG>
+__device__ __forceinline__ bool crossing_bond(const Bufs& b, const Lattice& lat, uint32_t t, int pos, uint64_t& a,
+                                              uint64_t& c, uint32_t& sa, uint32_t& sc) {
+  using R = TileRec<TH>;
+  uint64_t x0, y0;
+  int w, h;
+  tile_geom(lat, t, TH, x0, y0, w, h);
+  uint32_t tx, ty;
+  tile_xy(lat, t, tx, ty);
+  const bool right = pos < TH;
+  const int k = right ? pos : pos - TH;  // row of the right edge, or column of the bottom edge
+  const uint32_t tn = right ? ty * lat.ntx + (tx + 1 == lat.ntx ? 0u : tx + 1)
+                            : (ty + 1 == lat.nty ? 0u : ty + 1) * lat.ntx + tx;
+  const int ea = right ? k : 2 * TH + k;             // own right column / bottom row
+  const int ec = right ? TH + k : 2 * TH + kTW + k;  // the neighbour's left column / top row
+  const uint32_t* bw = b.ebits + (uint64_t)t * R::kBitWords + (right ? (k >> 5) : R::kRightWords + (k >> 5));
+  const uint16_t* pa = b.edge + (uint64_t)t * R::kEdge + ea;
+  const uint16_t* pc = b.edge + (uint64_t)tn * R::kEdge + ec;
+  const uint32_t word = kCG ? __ldcg(bw) : *bw;
+  sa = kCG ? __ldcg(pa) : *pa;
+  sc = kCG ? __ldcg(pc) : *pc;
+  a = (uint64_t)t * R::kOpenCap + sa;
+  c = (uint64_t)tn * R::kOpenCap + sc;
+  return k < (right ? h : w) && ((word >> (k & 31)) & 1u);
+}
+
+// End of a labelling pass: files the observables of the configuration the
+// labeller read into the ring, advances the lattice's sweep counter, and
+// (XY form) draws the sweep's embedding axis.
+__device__ __forceinline__ void file_sweep(const Bufs& b) {
+  const unsigned long long s = b.ctl[0];
+  if (b.measure) {
+    unsigned long long* rec = b.ring + (s % b.ring_cap) * (2ull + b.q);
+    rec[0] = s;
+    for (uint32_t k = 0; k <= b.q; ++k) {
+      rec[1 + k] = b.acc[k];
+      b.acc[k] = 0ull;
+    }
+  }
+  b.ctl[1] = s;
+  b.ctl[0] = s + 1ull;
+  if (b.M) b.ctl[2] = pick_state(stream4_rk(b.rk, 0ull, (uint32_t)s, kDomAxis).x, b.M);
+}
+
 // ================================================================== k_merge
 // One thread per edge position of every tile: TH right-edge rows, then the
 // 128 bottom-edge columns.  The thread at position 0 of a lattice's tile 0
-// also files the observables of the configuration k_label_tile read and
-// advances that lattice's sweep counter.
+// also files the sweep (file_sweep).
 template <int TH, typename LabelT, typename Src>
 __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__ Src src) {
-  using R = TileRec<TH>;
   constexpr int kPer = TH + kTW;
   const uint64_t item = (uint64_t)blockIdx.x * kMergeThreads + threadIdx.x;
   const uint32_t g = (uint32_t)(item / kPer);
@@ -1098,59 +1153,27 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__
   const Lattice& lat = src.lattice(rep);
   const uint32_t t = g - src.tile0(rep);
   if (g < src.ntiles()) {
-    uint64_t x0, y0;
-    int w, h;
-    tile_geom(lat, t, TH, x0, y0, w, h);
-    uint32_t tx, ty;
-    tile_xy(lat, t, tx, ty);
-    const uint32_t* bits = b.ebits + (uint64_t)t * R::kBitWords;
-    const uint16_t* edge = b.edge + (uint64_t)t * R::kEdge;
-    if (pos < TH) {
-      const int ly = pos;
-      if (ly < h && ((bits[ly >> 5] >> (ly & 31)) & 1u)) {
-        const uint32_t tn = ty * lat.ntx + (tx + 1 == lat.ntx ? 0u : tx + 1);
-        const uint32_t sa = edge[ly], sc = b.edge[(uint64_t)tn * R::kEdge + TH + ly];
-        a = (uint64_t)t * R::kOpenCap + sa;
-        c = (uint64_t)tn * R::kOpenCap + sc;
-        key = ((g & 1u) << 19) | (sa << kSlotBits) | sc;
-        active = true;
-      }
-    } else {
-      const int lx = pos - TH;
-      if (lx < w && ((bits[R::kRightWords + (lx >> 5)] >> (lx & 31)) & 1u)) {
-        const uint32_t tn = (ty + 1 == lat.nty ? 0u : ty + 1) * lat.ntx + tx;
-        const uint32_t sa = edge[2 * TH + lx], sc = b.edge[(uint64_t)tn * R::kEdge + 2 * TH + kTW + lx];
-        a = (uint64_t)t * R::kOpenCap + sa;
-        c = (uint64_t)tn * R::kOpenCap + sc;
-        key = ((g & 1u) << 19) | (1u << 18) | (sa << kSlotBits) | sc;
-        active = true;
-      }
-    }
+    uint32_t sa, sc;
+    active = crossing_bond<TH, false>(b, lat, t, pos, a, c, sa, sc);
+    key = ((g & 1u) << 19) | ((pos < TH ? 0u : 1u) << 18) | (sa << kSlotBits) | sc;
   }
   // neighbouring edge sites usually repeat the same pair of roots: one lane
   // per distinct (a, c) pair does the union.  A warp's positions lie in at
   // most two consecutive global tiles g (TH + 128 >= 32 positions each), so
   // g's parity, the edge (right or bottom) and the two open slots name the
   // pair.
-  const unsigned same = __match_any_sync(0xFFFFFFFFu, key);
+  const unsigned same = __match_any_sync(0xFFFFFFFFu, active ? key : 0xFFFFFFFFu);
   if (active && (int)(threadIdx.x & 31) == __ffs(same) - 1)
     gunite<TH>(b.G, lat, a, c, b.err, b.walk_cap ? b.walk_cap : kFindCap);
+  if (g < src.ntiles() && t == 0 && pos == 0) file_sweep(b);
+}
 
-  if (g < src.ntiles() && t == 0 && pos == 0) {
-    const unsigned long long s = b.ctl[0];
-    if (b.measure) {
-      unsigned long long* rec = b.ring + (s % b.ring_cap) * (2ull + b.q);
-      rec[0] = s;
-      for (uint32_t k = 0; k <= b.q; ++k) {
-        rec[1 + k] = b.acc[k];
-        b.acc[k] = 0ull;
-      }
-    }
-    b.ctl[1] = s;
-    b.ctl[0] = s + 1ull;
-    // XY form: the sweep's embedding axis, for the reflections
-    if (b.M) b.ctl[2] = pick_state(stream4_rk(b.rk, 0ull, (uint32_t)s, kDomAxis).x, b.M);
-  }
+// The sweep's filing when the labeller did the boundary unions (fused
+// merge schedule): a thread per lattice.
+template <typename Src>
+__global__ void k_file(const __grid_constant__ Src src) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < src.nreps()) file_sweep(src.bufs(r));
 }
 
 // ================================================================== k_resolve
@@ -1176,10 +1199,14 @@ __global__ void __launch_bounds__(kResolveThreads) k_resolve(const __grid_consta
   const uint32_t rep = src.rep(g);
   const Bufs& b = src.bufs(rep);
   const uint32_t t = g - src.tile0(rep);
-  if (k >= min(b.ocnt[t], (uint32_t)R::kOpenCap)) return;
-  const Lattice& lat = src.lattice(rep);
+  // the node's word is loaded with the tile's count (a slot past the count
+  // holds a stale word that is not used)
   const uint64_t d = (uint64_t)t * R::kOpenCap + k;
-  const uint64_t r = gfind<TH>(b.G, lat, d, ldcg(b.G + d), b.err, b.walk_cap ? b.walk_cap : kFindCap);
+  const uint32_t n = b.ocnt[t];
+  const uint64_t w = ldcg(b.G + d);
+  if (k >= min(n, (uint32_t)R::kOpenCap)) return;
+  const Lattice& lat = src.lattice(rep);
+  const uint64_t r = gfind<TH>(b.G, lat, d, w, b.err, b.walk_cap ? b.walk_cap : kFindCap);
   b.nso[d] = (uint8_t)pick_state(stream4_rk(b.rk, gsite(lat, r), (uint32_t)b.ctl[1], kDomSpin).x, b.q);
 }
 

@@ -936,6 +936,55 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
       }
       if (tid == 0) b.ocnt[t] = wcnt[0];
     }
+
+    // ================================================= M: boundary unions (fused merge schedule)
+    // Each tile edge is shared by two tiles; the one that finishes second
+    // unites the clusters across it, so k_merge is not needed.  A tile
+    // makes its records (nodes, edge slots, cross bits) visible to every SM,
+    // then counts each of its four edges with an atomicAdd; every sweep adds
+    // two to every counter, so the counter's old value is odd for the
+    // second tile, which then reads the other tile's records (loads that
+    // bypass L1) and does the unions of k_merge for that edge.  Nothing
+    // waits for another CTA.
+    if (!kGiven && b.fuse) {
+      uint32_t tx, ty;
+      tile_xy(lat, t, tx, ty);
+      const uint32_t tl = ty * lat.ntx + (tx == 0 ? lat.ntx - 1 : tx - 1);  // owner of the left edge
+      const uint32_t tt = (ty == 0 ? lat.nty - 1 : ty - 1) * lat.ntx + tx;  // owner of the top edge
+      __threadfence();
+      __syncthreads();  // every thread's records are out
+      if (tid < 4) {
+        const uint32_t ce = tid == 0 ? 2 * t : (tid == 1 ? 2 * t + 1 : (tid == 2 ? 2 * tl : 2 * tt + 1));
+        const uint32_t old = atomicAdd(b.ecnt + ce, 1u);
+        __threadfence();
+        reinterpret_cast<volatile uint8_t*>(wcnt + 1)[tid] = (uint8_t)(old & 1u);
+      }
+      __syncthreads();
+      const uint32_t f = wcnt[1];  // byte e: this tile unites across edge e
+      const int n0 = (f & 1u) ? h : 0, n1 = ((f >> 8) & 1u) ? w : 0;
+      const int n2 = ((f >> 16) & 1u) ? h : 0, n3 = ((f >> 24) & 1u) ? w : 0;
+      const int ntot = n0 + n1 + n2 + n3;
+      const uint32_t cap = b.walk_cap ? b.walk_cap : kFindCap;
+      for (int i0 = 0; i0 < ntot; i0 += kThreads) {  // CTA-uniform
+        const int i = i0 + tid;
+        uint64_t na = 0, nc = 0;
+        uint32_t key = 0xFFFFFFFFu;
+        bool act = false;
+        if (i < ntot) {
+          // edge e: 0 this tile's right, 1 its bottom, 2 the left (tl's
+          // right), 3 the top (tt's bottom); k: row or column along it
+          const int e = i < n0 ? 0 : (i < n0 + n1 ? 1 : (i < n0 + n1 + n2 ? 2 : 3));
+          const int k = i - (e > 0 ? n0 : 0) - (e > 1 ? n1 : 0) - (e > 2 ? n2 : 0);
+          const uint32_t owner = e < 2 ? t : (e == 2 ? tl : tt);
+          uint32_t sa, sc;
+          act = crossing_bond<TH, true>(b, lat, owner, (e & 1) ? TH + k : k, na, nc, sa, sc);
+          key = ((uint32_t)e << 18) | (sa << kSlotBits) | sc;
+        }
+        // one lane per distinct pair of nodes in the warp does the union
+        const unsigned same = __match_any_sync(kFull, act ? key : 0xFFFFFFFFu);
+        if (act && lane == __ffs(same) - 1) gunite<TH>(b.G, lat, na, nc, b.err, cap);
+      }
+    }
     // a replica's observables go out when the CTA's next tile belongs to
     // another replica (or there is none)
     if (Src::kMulti && measure) {

@@ -114,6 +114,13 @@ cudaError_t launch_merge_src(const Src& src, uint32_t ntiles, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// The sweep's filing after a labelling that did the boundary unions itself.
+template <typename Src>
+cudaError_t launch_file_src(const Src& src, uint32_t nreps, cudaStream_t st) {
+  k_file<Src><<<(nreps + 127) / 128, 128, 0, st>>>(src);
+  return cudaGetLastError();
+}
+
 template <int TH, typename LabelT, typename Src>
 cudaError_t launch_resolve_src(const Src& src, uint32_t ntiles, cudaStream_t st) {
   const uint64_t blocks = (uint64_t)ntiles * ResolveGrid<TH>::kPer;
@@ -131,14 +138,21 @@ cudaError_t launch_recolor_src(const Src& src, uint32_t ntiles, LabelT* roots, c
 // One full sweep (four launches) of every lattice the source names; `ev`
 // (four events or null) is recorded before, between and after the phases.
 // kXY: the embedded-cluster sweep of the XY model (Potts kernels with the
-// XY bond rule and reflections).
+// XY bond rule and reflections).  fused: the labeller does the boundary
+// unions (its lattices' Bufs::fuse set, edge counters allocated), and a
+// one-block filing kernel replaces k_merge.
 template <int TH, typename LabelT, typename Src, bool kXY = false>
-cudaError_t sweep_src(const Src& src, uint32_t ntiles, cudaStream_t st, cudaEvent_t* ev) {
+cudaError_t sweep_src(const Src& src, uint32_t ntiles, uint32_t nreps, bool fused, cudaStream_t st,
+                      cudaEvent_t* ev) {
   cudaError_t e;
   if (ev && (e = cudaEventRecord(ev[0], st))) return e;
   if ((e = launch_label_src<TH, LabelT, false, false, Src, kXY>(src, ntiles, st))) return e;
   if (ev && (e = cudaEventRecord(ev[1], st))) return e;
-  if ((e = launch_merge_src<TH, LabelT>(src, ntiles, st))) return e;
+  if (fused && !kXY) {
+    if ((e = launch_file_src(src, nreps, st))) return e;
+  } else {
+    if ((e = launch_merge_src<TH, LabelT>(src, ntiles, st))) return e;
+  }
   if ((e = launch_resolve_src<TH, LabelT>(src, ntiles, st))) return e;
   if (ev && (e = cudaEventRecord(ev[2], st))) return e;
   if ((e = launch_recolor_src<TH, LabelT, false, Src, kXY>(src, ntiles, (LabelT*)nullptr, st))) return e;
@@ -148,13 +162,14 @@ cudaError_t sweep_src(const Src& src, uint32_t ntiles, cudaStream_t st, cudaEven
 
 // Dispatch on the tile height.
 template <typename LabelT, typename Src, bool kXY = false>
-cudaError_t sweep_th(uint32_t th, const Src& src, uint32_t ntiles, cudaStream_t st, cudaEvent_t* ev) {
+cudaError_t sweep_th(uint32_t th, const Src& src, uint32_t ntiles, cudaStream_t st, cudaEvent_t* ev,
+                     uint32_t nreps = 1, bool fused = false) {
   switch (th) {
-    case 16: return sweep_src<16, LabelT, Src, kXY>(src, ntiles, st, ev);
-    case 32: return sweep_src<32, LabelT, Src, kXY>(src, ntiles, st, ev);
-    case 64: return sweep_src<64, LabelT, Src, kXY>(src, ntiles, st, ev);
+    case 16: return sweep_src<16, LabelT, Src, kXY>(src, ntiles, nreps, fused, st, ev);
+    case 32: return sweep_src<32, LabelT, Src, kXY>(src, ntiles, nreps, fused, st, ev);
+    case 64: return sweep_src<64, LabelT, Src, kXY>(src, ntiles, nreps, fused, st, ev);
     case 128:
-      if constexpr (!kXY) return sweep_src<128, LabelT, Src, false>(src, ntiles, st, ev);
+      if constexpr (!kXY) return sweep_src<128, LabelT, Src, false>(src, ntiles, nreps, fused, st, ev);
       else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }

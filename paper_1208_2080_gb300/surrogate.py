@@ -154,7 +154,21 @@ def peak_estimate(T, chi):
     return float(v) if T[a] <= v <= T[b - 1] else float(T[k])
 
 
-def train_on_batch(R=512, sweeps=1000, master_seed=6, steps=3000, seed=0):
+def peak_estimate_dense(T, chi, frac=0.7):
+    """Peak of chi(T) from a dense grid: vertex of the least-squares parabola
+    in T through log chi at every point whose chi is at least `frac` of the
+    largest (many points, so the noise of single points averages out)."""
+    T = np.asarray(T, dtype=np.float64)
+    chi = np.asarray(chi, dtype=np.float64)
+    sel = chi >= frac * chi.max()
+    if sel.sum() < 3:
+        return float(T[int(np.argmax(chi))])
+    c2, c1, _ = np.polyfit(T[sel], np.log(chi[sel]), 2)
+    v = -c1 / (2 * c2) if c2 < 0 else float(T[int(np.argmax(chi))])
+    return float(min(max(v, T[0]), T[-1]))
+
+
+def train_on_batch(R=512, sweeps=2000, master_seed=6, steps=3000, seed=0):
     """Training set from one batched run (the replica mix of synth.replica_batch)
     and a trained Surrogate."""
     p = synth.replica_batch(R, master_seed=master_seed)
@@ -166,10 +180,14 @@ def train_on_batch(R=512, sweeps=1000, master_seed=6, steps=3000, seed=0):
     return model, {"R": R, "sweeps": sweeps, "run_s": dt, "final_loss": model.losses[-1][1]}
 
 
-def compare_grids(model, qs=(2, 3, 4), Ls=(512, 1024, 2048), n=32, sweeps=5000, master_seed=7):
+def compare_grids(model, qs=(2, 3, 4), Ls=(512, 1024, 2048), n=32, sweeps=5000, master_seed=7,
+                  dense=96, dense_halfwidth=0.015):
     """For every (q, L): measure chi on the surrogate-placed grid and on the
-    plain uniform grid (one batch each), estimate both peaks, and report the
-    surrogate's prediction error at the placed temperatures."""
+    plain uniform grid (one batch each), estimate both peaks, and judge both
+    against a dense reference grid (`dense` temperatures over +-`dense_halfwidth`
+    around the uniform grid's estimate, the same sweeps; 0 skips it); report
+    the surrogate's prediction error at the placed temperatures and at the
+    peak."""
     rng = np.random.Generator(np.random.PCG64(master_seed))
     cells = [(q, L) for q in qs for L in Ls]
     grids, info = {}, {}
@@ -187,6 +205,24 @@ def compare_grids(model, qs=(2, 3, 4), Ls=(512, 1024, 2048), n=32, sweeps=5000, 
         obs, dt = measure_batch(np.array(Lb, np.uint64), np.array(qb, np.uint32), np.array(Tb),
                                 seeds, sweeps)
         res[name] = (np.array(Tb), obs, dt)
+    # the judge: a dense grid around the uniform grid's estimate of every cell
+    ref = {}
+    if dense:
+        Tu_all, ou_all, _ = res["uniform"]
+        Lb, qb, Tb = [], [], []
+        for c, (q, L) in enumerate(cells):
+            sl = slice(c * n, (c + 1) * n)
+            pu = peak_estimate(Tu_all[sl], ou_all[sl, 2])
+            Lb += [L] * dense
+            qb += [q] * dense
+            Tb += list(np.linspace(pu * (1 - dense_halfwidth), pu * (1 + dense_halfwidth), dense))
+        seeds = rng.integers(0, 2 ** 63, size=len(Lb), dtype=np.uint64)
+        obs, dt = measure_batch(np.array(Lb, np.uint64), np.array(qb, np.uint32), np.array(Tb),
+                                seeds, sweeps)
+        res["dense"] = (np.array(Tb), obs, dt)
+        for c, cell in enumerate(cells):
+            sl = slice(c * dense, (c + 1) * dense)
+            ref[cell] = (res["dense"][0][sl], obs[sl])
     out = {"sweeps": sweeps, "cells": []}
     for c, (q, L) in enumerate(cells):
         sl = slice(c * n, (c + 1) * n)
@@ -210,15 +246,45 @@ def compare_grids(model, qs=(2, 3, 4), Ls=(512, 1024, 2048), n=32, sweeps=5000, 
             "pred_rmse_at_placed_T": {k: float(np.sqrt(np.mean((pred[:, i] - meas[:, i]) ** 2)))
                                       for i, k in enumerate(["u", "m", "log_chi", "U4"])},
         })
+        if (q, L) in ref:
+            Td, od = ref[(q, L)]
+            pd = peak_estimate_dense(Td, od[:, 2])
+            cell = out["cells"][-1]
+            cell["dense_reference"] = {
+                "points": int(len(Td)), "spacing_over_Tc": float((Td[1] - Td[0]) / tc),
+                "peak_T_over_Tc": pd / tc,
+                # chi-peak errors of the two grids against the dense reference
+                "rel_err_surrogate_grid": abs(ps - pd) / pd,
+                "rel_err_uniform_grid": abs(pu - pd) / pd,
+            }
+            # the network against the reference: its predicted peak, next to
+            # the infinite-volume T_c as a predictor, and its RMSE within
+            # +-0.5% of the peak
+            near = np.abs(Td - pd) <= 0.005 * pd
+            predd = model.predict(features(np.full(int(near.sum()), q), np.full(int(near.sum()), L), Td[near]))
+            measd = targets(od[near])
+            t_pred = info[(q, L)].get("t_peak_pred")
+            cell["network_at_peak"] = {
+                "peak_rel_err_predicted": (abs(t_pred * tc - pd) / pd) if t_pred is not None else None,
+                "peak_rel_err_Tc": abs(tc - pd) / pd,
+                "rmse_within_0.5pct": {k: float(np.sqrt(np.mean((predd[:, i] - measd[:, i]) ** 2)))
+                                       for i, k in enumerate(["u", "m", "log_chi", "U4"])},
+                "points": int(near.sum()),
+            }
     out["run_s"] = {k: v[2] for k, v in res.items()}
     out["max_rel_diff"] = max(c["rel_diff"] for c in out["cells"])
+    if ref:
+        out["max_rel_err_surrogate_grid"] = max(c["dense_reference"]["rel_err_surrogate_grid"]
+                                                for c in out["cells"])
+        out["max_rel_err_uniform_grid"] = max(c["dense_reference"]["rel_err_uniform_grid"]
+                                              for c in out["cells"])
     return out
 
 
 def main():
     import argparse
     ap = argparse.ArgumentParser(description="train the surrogate and compare temperature grids")
-    ap.add_argument("--train-sweeps", type=int, default=1000)
+    ap.add_argument("--train-sweeps", type=int, default=2000)
     ap.add_argument("--sweeps", type=int, default=5000)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--out", default=None)

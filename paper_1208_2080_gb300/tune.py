@@ -1,8 +1,10 @@
 """Autotuner for the batched replica runner.
 
 Chooses, for a given batch (its mix of lattice sizes), the labelling tile
-height (16, 32 or 64 rows of 128 sites) and whether a batch sweep is
-replayed as a CUDA graph or launched directly, by timing a few sweeps of
+height (32, 64 or 128 rows of 128 sites), the merge schedule (the boundary
+unions in a kernel of their own, or done by the labeller itself: the tile
+that finishes second unites across a shared edge) and whether a batch sweep
+is replayed as a CUDA graph or launched directly, by timing a few sweeps of
 each candidate with CUDA events.  Results are cached in a JSON file keyed by
 the GPU name and the batch's size histogram.  Choices never change results:
 every candidate is bit-identical (tests check that), only speed differs.
@@ -15,7 +17,7 @@ import numpy as np
 
 from ._binding import Batch
 
-CANDIDATES = [(th, g) for th in (64, 32, 16) for g in (True, False)]
+CANDIDATES = [(th, g, m) for th in (128, 64, 32) for m in ("kernel", "fused") for g in (True, False)]
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "swgb", "tune.json")
 
 
@@ -32,10 +34,10 @@ def _load(path):
         return {}
 
 
-def time_batch(L, q, T, seed, tile_h, graph, sweeps=4, warmup=2):
+def time_batch(L, q, T, seed, tile_h, graph, merge="kernel", sweeps=4, warmup=2):
     """Mean device milliseconds per batch sweep for one candidate."""
     import torch
-    with Batch(L, q, T, seed, tile_h=tile_h, graph=graph) as b:
+    with Batch(L, q, T, seed, tile_h=tile_h, graph=graph, merge=merge) as b:
         b.sweep(warmup)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -48,8 +50,8 @@ def time_batch(L, q, T, seed, tile_h, graph, sweeps=4, warmup=2):
 
 
 def tune_batch(L, q, T, seed, *, cache=DEFAULT_CACHE, sweeps=4, force=False, candidates=None):
-    """Returns {"tile_h": .., "graph": .., "ms_per_sweep": .., "timings": [...]} for the
-    batch, measuring (and caching) if needed."""
+    """Returns {"tile_h": .., "graph": .., "merge": .., "ms_per_sweep": .., "timings": [...]}
+    for the batch, measuring (and caching) if needed."""
     import torch
     gpu = torch.cuda.get_device_name()
     key = _key(L, gpu)
@@ -57,13 +59,13 @@ def tune_batch(L, q, T, seed, *, cache=DEFAULT_CACHE, sweeps=4, force=False, can
     if not force and key in db:
         return db[key]
     timings = []
-    for th, g in (candidates or CANDIDATES):
+    for th, g, m in (candidates or CANDIDATES):
         t0 = time.time()
-        ms = time_batch(L, q, T, seed, th, g, sweeps=sweeps)
-        timings.append({"tile_h": th, "graph": g, "ms_per_sweep": ms, "wall_s": time.time() - t0})
+        ms = time_batch(L, q, T, seed, th, g, m, sweeps=sweeps)
+        timings.append({"tile_h": th, "graph": g, "merge": m, "ms_per_sweep": ms, "wall_s": time.time() - t0})
     best = min(timings, key=lambda x: x["ms_per_sweep"])
-    res = {"tile_h": best["tile_h"], "graph": best["graph"], "ms_per_sweep": best["ms_per_sweep"],
-           "timings": timings}
+    res = {"tile_h": best["tile_h"], "graph": best["graph"], "merge": best["merge"],
+           "ms_per_sweep": best["ms_per_sweep"], "timings": timings}
     db[key] = res
     try:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
@@ -76,6 +78,7 @@ def tune_batch(L, q, T, seed, *, cache=DEFAULT_CACHE, sweeps=4, force=False, can
 
 
 def tuned_batch(L, q, T, seed, **kw):
-    """A Batch built with the tuned tile height and launch mode."""
+    """A Batch built with the tuned tile height, merge schedule and launch mode."""
     cfg = tune_batch(L, q, T, seed)
-    return Batch(L, q, T, seed, tile_h=cfg["tile_h"], graph=cfg["graph"], **kw), cfg
+    return Batch(L, q, T, seed, tile_h=cfg["tile_h"], graph=cfg["graph"],
+                 merge=cfg.get("merge", "kernel"), **kw), cfg

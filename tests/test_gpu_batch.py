@@ -22,11 +22,13 @@ MIXED = dict(
 )
 
 
-@pytest.mark.parametrize("tile_h,graph", [(64, True), (32, False), (16, True)])
-def test_mixed_batch_matches_oracle(tile_h, graph):
+@pytest.mark.parametrize("tile_h,graph,merge", [(64, True, "fused"), (32, False, "kernel"), (16, True, "fused"),
+                                               (128, True, "kernel"), (128, False, "fused")])
+def test_mixed_batch_matches_oracle(tile_h, graph, merge):
     n = 9
     with sw.Batch(MIXED["L"], MIXED["q"], MIXED["T"], MIXED["seed"], tile_h=tile_h,
-                  graph=graph) as b:
+                  graph=graph, merge=merge) as b:
+        assert b.info()["merge"] == sw._binding.MERGE[merge]
         b.sweep(n)
         for r in range(len(MIXED["L"])):
             L, q, T, seed = (MIXED[k][r] for k in ("L", "q", "T", "seed"))

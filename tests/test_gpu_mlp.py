@@ -202,8 +202,11 @@ def test_training_reduces_loss_on_a_smooth_target():
 def test_surrogate_grid_finds_the_peak_and_resolves_it():
     """Trained on a batched run of 512 mixed replicas, the network places 32
     temperatures for (q=2, L=512); the chi-peak estimated from sweeps at
-    those temperatures agrees with the plain uniform grid's within 1%, and
-    the placed grid samples the peak several times more densely."""
+    those temperatures agrees with the plain uniform grid's within 1%, the
+    placed grid samples the peak several times more densely, and -- judged
+    against a dense reference grid of 96 temperatures at the same sweeps --
+    its peak is at least as close to the reference as the uniform grid's
+    (within the reference's own spacing), and within 1%."""
     from paper_1208_2080_gb300 import surrogate as sg
     model, info = sg.train_on_batch(R=512, sweeps=400, steps=2000)
     res = sg.compare_grids(model, qs=(2,), Ls=(512,), sweeps=2000)
@@ -212,6 +215,9 @@ def test_surrogate_grid_finds_the_peak_and_resolves_it():
     assert c["rel_diff"] < 0.01, c
     assert c["grid_spacing_over_Tc"]["surrogate"] * 3 < c["grid_spacing_over_Tc"]["uniform"]
     assert c["points_above_half_max"]["surrogate"] >= 3 * c["points_above_half_max"]["uniform"]
+    d = c["dense_reference"]
+    assert d["rel_err_surrogate_grid"] < 0.01, d
+    assert d["rel_err_surrogate_grid"] <= max(d["rel_err_uniform_grid"], 2 * d["spacing_over_Tc"]), d
     model.close()
 
 

@@ -93,11 +93,13 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("merge", ["fused", "kernel"])
 @pytest.mark.parametrize("L,q,T", CASES)
-def test_sweeps_bit_exact(L, q, T):
+def test_sweeps_bit_exact(L, q, T, merge):
     T = sw.tc(q) if T is None else T
     seed, n = 7 * L + q, 12
-    with sw.Sim(L, q, T, seed) as s:
+    with sw.Sim(L, q, T, seed, merge=merge) as s:
+        assert s.info()["merge"] == sw._binding.MERGE[merge]
         s.sweep(n)
         got = s.spins()
         E, nn = s.series(0, n + 1)
@@ -109,15 +111,16 @@ def test_sweeps_bit_exact(L, q, T):
     assert np.array_equal(nn[1:], refn)
 
 
-@pytest.mark.parametrize("L", [96, 250])
-def test_results_independent_of_tile_and_label_width(L):
+@pytest.mark.parametrize("L", [96, 250, 1000])
+def test_results_independent_of_tile_label_width_and_merge_schedule(L):
     q, T, seed, n = 3, sw.tc(3), 4242, 6
     outs = []
     for th in TILE_HS:
         for bits in (32, 64):
-            with sw.Sim(L, q, T, seed, tile_h=th, label_bits=bits) as s:
-                s.sweep(n)
-                outs.append((s.spins(), s.series(0, n + 1)))
+            for merge in ("fused", "kernel"):
+                with sw.Sim(L, q, T, seed, tile_h=th, label_bits=bits, merge=merge) as s:
+                    s.sweep(n)
+                    outs.append((s.spins(), s.series(0, n + 1)))
     for sp, (E, nn) in outs[1:]:
         assert np.array_equal(sp, outs[0][0])
         assert np.array_equal(E, outs[0][1][0]) and np.array_equal(nn, outs[0][1][1])
