@@ -60,6 +60,30 @@ __device__ __forceinline__ Words4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uin
   return Words4{c0, c1, c2, c3};
 }
 
+// Same function with the round keys in shared memory, two rounds' keys per
+// 16-byte load (k4[i] = keys of rounds 2i and 2i+1).
+__device__ __forceinline__ Words4 philox4x32_10_k4(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                   const uint4* k4) {
+  constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const uint4 k = k4[i];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint64_t p0 = (uint64_t)kMul0 * c0, p1 = (uint64_t)kMul1 * c2;
+      const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+      const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+      const uint32_t n0 = hi1 ^ c1 ^ (h ? k.z : k.x);
+      const uint32_t n2 = hi0 ^ c3 ^ (h ? k.w : k.y);
+      c0 = n0;
+      c1 = lo1;
+      c2 = n2;
+      c3 = lo0;
+    }
+  }
+  return Words4{c0, c1, c2, c3};
+}
+
 // Stream domains (fourth counter word).
 enum : uint32_t { kDomBond = 0, kDomSpin = 1, kDomInit = 2, kDomAxis = 3 };
 

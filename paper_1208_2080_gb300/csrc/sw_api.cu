@@ -319,8 +319,10 @@ cudaError_t sweep_banded(sw_sim* s, const uint32_t* r, uint32_t nb) {
   for (uint32_t bnd = 0; bnd < nb; ++bnd) {
     if ((e = cudaStreamWaitEvent(s->stream, s->up_ev[bnd], 0))) return e;
     const BandSrc src{s->b, lat, r[bnd] * lat.ntx, (r[bnd + 1] - r[bnd]) * lat.ntx};
-    if ((e = launch_label_src<TH, LabelT, false, false>(src, (r[bnd + 1] - r[bnd]) * lat.ntx, s->stream)))
-      return e;
+    const uint32_t n = (r[bnd + 1] - r[bnd]) * lat.ntx;
+    e = s->b.fuse ? launch_label_src<TH, LabelT, false, false, BandSrc, false, true>(src, n, s->stream)
+                  : launch_label_src<TH, LabelT, false, false>(src, n, s->stream);
+    if (e) return e;
   }
   const SingleSrc full{s->b, lat};
   if (s->b.fuse) {

@@ -94,8 +94,8 @@ cudaError_t batch_sweep_once(sw_batch* b, cudaStream_t st, cudaEvent_t* ev) {
 // sweep).
 int build_graph(sw_batch* b) {
   const BatchSrc src{b->d_reps, b->d_tile_rep, b->total, b->R};
-  cudaError_t e = b->label_bits == 64 ? configure_th<uint64_t, BatchSrc>(b->th, src)
-                                      : configure_th<uint32_t, BatchSrc>(b->th, src);
+  cudaError_t e = b->label_bits == 64 ? configure_th<uint64_t, BatchSrc>(b->th, src, b->fuse)
+                                      : configure_th<uint32_t, BatchSrc>(b->th, src, b->fuse);
   if (e != cudaSuccess) return bcuda(b, e);
   if (!b->cap_stream) {
     e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);

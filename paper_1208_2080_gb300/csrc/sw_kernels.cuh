@@ -1223,8 +1223,24 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const __grid_constant__ Sr
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t g = blockIdx.x;
   const uint32_t rep = src.rep(g);
-  const Bufs& b = src.bufs(rep);
-  const Lattice& lat = src.lattice(rep);
+  // a replica batch: the block's replica record once, through shared memory
+  // (each thread reading it from the replica table would wait on a chain of
+  // loads before streaming)
+  __shared__ __align__(16) unsigned char srec[Src::kMulti ? sizeof(Rep) : 16];
+  if constexpr (Src::kMulti) {
+    const uint32_t* from = reinterpret_cast<const uint32_t*>(&src.bufs(rep));
+    for (int k = tid; k < (int)(sizeof(Rep) / 4); k += kThreads)
+      reinterpret_cast<uint32_t*>(srec)[k] = __ldg(from + k);
+    __syncthreads();
+  }
+  const Bufs& b = [&]() -> const Bufs& {
+    if constexpr (Src::kMulti) return reinterpret_cast<const Rep*>(srec)->b;
+    else return src.bufs(rep);
+  }();
+  const Lattice& lat = [&]() -> const Lattice& {
+    if constexpr (Src::kMulti) return reinterpret_cast<const Rep*>(srec)->lat;
+    else return src.lattice(rep);
+  }();
   const uint32_t t = g - src.tile0(rep);
   uint64_t x0, y0;
   int w, h;

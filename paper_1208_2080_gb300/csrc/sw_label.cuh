@@ -237,7 +237,9 @@ __device__ __forceinline__ void stage_rows(const Src& src, uint32_t gg, uint8_t*
 //
 // kGiven: bonds are read from b.bonds instead of drawn (labelling-only entry).
 // kRoots: closed clusters keep their local root in the code (no new state).
-template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src>
+// kFuse: the labeller also does the boundary unions (phase M; the fused
+// merge schedule).
+template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kFuse = false>
 __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
     k_label_rows(const __grid_constant__ Src src) {
   using C = RowCta<TH>;
@@ -256,6 +258,12 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
   uint32_t* cbits = reinterpret_cast<uint32_t*>(smem + S::kCb);
   uint32_t* wcnt = reinterpret_cast<uint32_t*>(smem + S::kCnt);
   uint32_t* sobs = reinterpret_cast<uint32_t*>(smem + S::kObs);
+  // replica batch: the current tile's replica record (buffers, Philox round
+  // keys, geometry), two copies by tile parity.  A lattice of its own has
+  // these among the kernel parameters, as free constant operands; read from
+  // the replica table in global memory they would take registers.
+  __shared__ __align__(16) unsigned char srec[Src::kMulti ? 2 * sizeof(Rep) : 16];
+  __shared__ __align__(16) uint32_t srk[Src::kMulti ? 2 * 20 : 4];  // its Philox round keys, 16-byte aligned
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int part = lane % kLpr;
@@ -304,6 +312,30 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
     nsites = 0;
     ncnt[0] = ncnt[1] = ncnt[2] = 0;
   };
+  // The same for one tile's bit-plane counts (q <= 4), warp by warp: a
+  // warp's sites are its rows of the tile, n[0] the rest of them.
+  auto warp_flush = [&](const Bufs& fb, uint32_t fq, int fw, int fh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e_loc += __shfl_xor_sync(kFull, e_loc, o);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ncnt[k] += __shfl_xor_sync(kFull, ncnt[k], o);
+    if (lane == 0) {
+      const int nr = min(max(fh - warp * kRpw, 0), kRpw);
+      const uint32_t n1 = ncnt[0] - ncnt[2];
+      const uint32_t n2 = fq > 2 ? ncnt[1] - ncnt[2] : 0u;
+      const uint32_t n3 = fq > 3 ? ncnt[2] : 0u;
+      atomicAdd(&fb.acc[0], (unsigned long long)e_loc);
+      atomicAdd(&fb.acc[1], (unsigned long long)((uint32_t)(nr * fw) - n1 - n2 - n3));
+      atomicAdd(&fb.acc[2], (unsigned long long)n1);
+      if (fq > 2) atomicAdd(&fb.acc[3], (unsigned long long)n2);
+      if (fq > 3) atomicAdd(&fb.acc[4], (unsigned long long)n3);
+    }
+    e_loc = 0;
+    if (tid == 0) nsites = 0;
+    ncnt[0] = ncnt[1] = ncnt[2] = 0;
+  };
 
   bool pre = false;
   if (!kGiven && blockIdx.x < total && src.lattice(src.rep(blockIdx.x)).vec4) {
@@ -312,24 +344,45 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
     pre = true;
   }
 
-  for (uint32_t g = blockIdx.x; g < total; g += gridDim.x) {
+  uint32_t par = 0;  // tile parity: the shared copy of the replica record in use (batch)
+  for (uint32_t g = blockIdx.x; g < total; g += gridDim.x, par ^= 1u) {
     const uint32_t rep = src.rep(g);
-    const Bufs& b = src.bufs(rep);
-    const Lattice& lat = src.lattice(rep);
+    if constexpr (Src::kMulti) {
+      // the other copy may still be read by the previous tile's last phase
+      const uint32_t* from = reinterpret_cast<const uint32_t*>(src.reps + rep);
+      uint32_t* to = reinterpret_cast<uint32_t*>(srec + par * sizeof(Rep));
+      for (int k = tid; k < (int)(sizeof(Rep) / 4); k += kThreads) to[k] = __ldg(from + k);
+      if (tid < 20) srk[20 * par + tid] = src.reps[rep].b.rk[tid];
+    }
     const uint32_t t = g - src.tile0(rep);
-    const uint64_t L = lat.L;
-    const uint32_t q_states = b.q;
-    const bool measure = !kGiven && b.measure;
-    const uint32_t sweep = kGiven ? 0u : (uint32_t)b.ctl[0];
     uint64_t x0, y0;
     int w, h;
-    tile_geom(lat, t, TH, x0, y0, w, h);
+    tile_geom(src.lattice(rep), t, TH, x0, y0, w, h);
     if (!kGiven) {
       if (pre) cp_async_wait();
       else stage_rows<TH, kThreads>(src, g, sp, hal, false);
     }
     if (tid == 0) nsites += (uint32_t)(w * h);
     __syncthreads();  // staged spins visible; the previous tile is done with every shared array
+    const Bufs& b = [&]() -> const Bufs& {
+      if constexpr (Src::kMulti) return reinterpret_cast<const Rep*>(srec)[par].b;
+      else return src.bufs(rep);
+    }();
+    const Lattice& lat = [&]() -> const Lattice& {
+      if constexpr (Src::kMulti) return reinterpret_cast<const Rep*>(srec)[par].lat;
+      else return src.lattice(rep);
+    }();
+    const uint64_t L = lat.L;
+    const uint32_t q_states = b.q;
+    const bool measure = !kGiven && b.measure;
+    const uint32_t sweep = kGiven ? 0u : (uint32_t)b.ctl[0];
+    auto philox = [&](uint64_t idx, uint32_t dom) -> Words4 {
+      if constexpr (Src::kMulti)
+        return philox4x32_10_k4((uint32_t)idx, (uint32_t)(idx >> 32), sweep, dom,
+                                reinterpret_cast<const uint4*>(srk + 20 * par));
+      else return stream4_rk(b.rk, idx, sweep, dom);
+    };
+    const uint32_t thr = b.thr;
 
     // ================================================= A: bonds, observables, runs
     uint32_t vm[kW], H[kW], V[kW], Sm[kW], Cw[kW];
@@ -455,19 +508,19 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
           if (er | ed) {
             const uint64_t i0 = rowg + 32 * wi + sh;
             const uint64_t pa = i0 >> 1;
-            const Words4 A = stream4_rk(b.rk, pa, sweep, kDomBond);
-            const Words4 B = stream4_rk(b.rk, pa + 1, sweep, kDomBond);
+            const Words4 A = philox(pa, kDomBond);
+            const Words4 B = philox(pa + 1, kDomBond);
             uint32_t wr[4], wd[4];
             if ((i0 & 1u) == 0u) {
               wr[0] = A.x; wd[0] = A.y; wr[1] = A.z; wd[1] = A.w;
               wr[2] = B.x; wd[2] = B.y; wr[3] = B.z; wd[3] = B.w;
             } else {
-              const Words4 Cc = stream4_rk(b.rk, pa + 2, sweep, kDomBond);
+              const Words4 Cc = philox(pa + 2, kDomBond);
               wr[0] = A.z; wd[0] = A.w; wr[1] = B.x; wd[1] = B.y;
               wr[2] = B.z; wd[2] = B.w; wr[3] = Cc.x; wd[3] = Cc.y;
             }
-            br = er & lt_mask4(wr, b.thr);
-            bd = ed & lt_mask4(wd, b.thr);
+            br = er & lt_mask4(wr, thr);
+            bd = ed & lt_mask4(wd, thr);
             H[wi] |= br << sh;
             V[wi] |= bd << sh;
           }
@@ -819,7 +872,7 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
                 code = kMarkA | r;
               } else {
                 code = kMarkA |
-                       pick_state(stream4_rk(b.rk, global_index(lat, x0, y0, r), sweep, kDomSpin).x, q_states);
+                       pick_state(philox(global_index(lat, x0, y0, r), kDomSpin).x, q_states);
               }
               vp[r] = (uint16_t)code;
             }
@@ -946,7 +999,7 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
     // second tile, which then reads the other tile's records (loads that
     // bypass L1) and does the unions of k_merge for that edge.  Nothing
     // waits for another CTA.
-    if (!kGiven && b.fuse) {
+    if constexpr (kFuse && !kGiven) {
       uint32_t tx, ty;
       tile_xy(lat, t, tx, ty);
       const uint32_t tl = ty * lat.ntx + (tx == 0 ? lat.ntx - 1 : tx - 1);  // owner of the left edge
@@ -986,10 +1039,15 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
       }
     }
     // a replica's observables go out when the CTA's next tile belongs to
-    // another replica (or there is none)
+    // another replica (or there is none); with the bit-plane counts (q <= 4)
+    // each warp adds its own share at once, with no barrier
     if (Src::kMulti && measure) {
-      const uint32_t gn = g + gridDim.x;
-      if (gn >= total || src.rep(gn) != rep) flush(b, q_states);
+      if (q_states <= 4) {
+        warp_flush(b, q_states, w, h);
+      } else {
+        const uint32_t gn = g + gridDim.x;
+        if (gn >= total || src.rep(gn) != rep) flush(b, q_states);
+      }
     }
   }
 

@@ -62,11 +62,11 @@ int rows_smem(const Src& src) {
 }
 
 // Potts labeller (k_label_rows): attributes and resident CTAs on this device.
-template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src>
+template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kFuse>
 cudaError_t configure_rows(int smem, int* resident_out) {
   static std::atomic<int> resident[2][kMaxDevices];
   const int big = smem > RowSmem<TH>::kBytesSmallQ ? 1 : 0;
-  return configure_on_device(k_label_rows<TH, LabelT, kGiven, kRoots, Src>, RowCta<TH>::kThreads, smem,
+  return configure_on_device(k_label_rows<TH, LabelT, kGiven, kRoots, Src, kFuse>, RowCta<TH>::kThreads, smem,
                              RowSmem<TH>::kBytes, resident[big], resident_out);
 }
 
@@ -79,21 +79,21 @@ cudaError_t configure_tile(int* resident_out) {
                              smem, resident, resident_out);
 }
 
-template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY = false>
+template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY = false, bool kFuse = false>
 cudaError_t configure_label(const Src& src, int* resident_out) {
   if constexpr (kXY) {
     (void)src;
     return configure_tile<TH, LabelT, kGiven, kRoots, Src, kXY>(resident_out);
   } else {
-    return configure_rows<TH, LabelT, kGiven, kRoots, Src>(rows_smem<TH, kGiven>(src), resident_out);
+    return configure_rows<TH, LabelT, kGiven, kRoots, Src, kFuse>(rows_smem<TH, kGiven>(src), resident_out);
   }
 }
 
 // One labelling launch: a persistent grid of as many tile CTAs as fit.
-template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY = false>
+template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY = false, bool kFuse = false>
 cudaError_t launch_label_src(const Src& src, uint32_t ntiles, cudaStream_t st) {
   int resident = 0;
-  cudaError_t e = configure_label<TH, LabelT, kGiven, kRoots, Src, kXY>(src, &resident);
+  cudaError_t e = configure_label<TH, LabelT, kGiven, kRoots, Src, kXY, kFuse>(src, &resident);
   if (e != cudaSuccess) return e;
   const uint32_t grid = ntiles < (uint32_t)resident ? ntiles : (uint32_t)resident;
   if (grid == 0) return cudaSuccess;
@@ -101,7 +101,8 @@ cudaError_t launch_label_src(const Src& src, uint32_t ntiles, cudaStream_t st) {
     k_label_tile<TH, LabelT, kGiven, kRoots, Src, kXY>
         <<<grid, TileCta<TH>::kThreads, LabelSmem<TH>::kXYBytes, st>>>(src);
   } else {
-    k_label_rows<TH, LabelT, kGiven, kRoots, Src><<<grid, RowCta<TH>::kThreads, rows_smem<TH, kGiven>(src), st>>>(src);
+    k_label_rows<TH, LabelT, kGiven, kRoots, Src, kFuse>
+        <<<grid, RowCta<TH>::kThreads, rows_smem<TH, kGiven>(src), st>>>(src);
   }
   return cudaGetLastError();
 }
@@ -146,7 +147,9 @@ cudaError_t sweep_src(const Src& src, uint32_t ntiles, uint32_t nreps, bool fuse
                       cudaEvent_t* ev) {
   cudaError_t e;
   if (ev && (e = cudaEventRecord(ev[0], st))) return e;
-  if ((e = launch_label_src<TH, LabelT, false, false, Src, kXY>(src, ntiles, st))) return e;
+  if (fused && !kXY) e = launch_label_src<TH, LabelT, false, false, Src, false, true>(src, ntiles, st);
+  else e = launch_label_src<TH, LabelT, false, false, Src, kXY>(src, ntiles, st);
+  if (e) return e;
   if (ev && (e = cudaEventRecord(ev[1], st))) return e;
   if (fused && !kXY) {
     if ((e = launch_file_src(src, nreps, st))) return e;
@@ -176,12 +179,17 @@ cudaError_t sweep_th(uint32_t th, const Src& src, uint32_t ntiles, cudaStream_t 
 }
 
 template <typename LabelT, typename Src>
-cudaError_t configure_th(uint32_t th, const Src& src) {
+cudaError_t configure_th(uint32_t th, const Src& src, bool fused = false) {
   switch (th) {
-    case 16: return configure_label<16, LabelT, false, false, Src>(src, nullptr);
-    case 32: return configure_label<32, LabelT, false, false, Src>(src, nullptr);
-    case 64: return configure_label<64, LabelT, false, false, Src>(src, nullptr);
-    case 128: return configure_label<128, LabelT, false, false, Src>(src, nullptr);
+#define SWGB_CONF(THV)                                                                           \
+  case THV:                                                                                      \
+    return fused ? configure_label<THV, LabelT, false, false, Src, false, true>(src, nullptr)    \
+                 : configure_label<THV, LabelT, false, false, Src>(src, nullptr);
+    SWGB_CONF(16)
+    SWGB_CONF(32)
+    SWGB_CONF(64)
+    SWGB_CONF(128)
+#undef SWGB_CONF
     default: return cudaErrorInvalidValue;
   }
 }
