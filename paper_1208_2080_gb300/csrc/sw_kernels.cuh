@@ -1247,6 +1247,18 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const __grid_constant__ Sr
   tile_geom(lat, t, TH, x0, y0, w, h);
   const uint64_t L = lat.L;
   const uint8_t* nso = b.nso + (uint64_t)t * R::kOpenCap;
+  // kRoots: the global root of each of the tile's open roots, found once
+  // (a thread per open slot) instead of once per site of its cluster
+  __shared__ LabelT oroot[kRoots ? R::kOpenCap : 1];
+  if constexpr (kRoots) {
+    const uint32_t n = min(b.ocnt[t], (uint32_t)R::kOpenCap);
+    const uint32_t cap = b.walk_cap ? b.walk_cap : kFindCap;
+    for (uint32_t k = (uint32_t)tid; k < n; k += kThreads) {
+      const uint64_t d = (uint64_t)t * R::kOpenCap + k;
+      oroot[k] = (LabelT)gsite(lat, gfind<TH>(b.G, lat, d, ldcg(b.G + d), b.err, cap));
+    }
+    __syncthreads();
+  }
   uint32_t jx = 0, Mx = 0;
   if constexpr (kXY) {
     jx = (uint32_t)b.ctl[2];  // the sweep's embedding axis, filed by k_merge
@@ -1308,17 +1320,22 @@ __global__ void __launch_bounds__(kThreads) k_recolor(const __grid_constant__ Sr
         for (int k = 0; k < 4; ++k) c[k] = lx0 + k < w ? b.code[gi + k] : 0u;
       }
       if (kRoots) {
+        LabelT rv[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if (lx0 + k < w) {
-            if (c[k] & kClosed) {
-              roots[gi + k] = (LabelT)global_index(lat, x0, y0, c[k] & kIdx);
-            } else {
-              const uint64_t d = (uint64_t)t * R::kOpenCap + c[k];
-              const uint64_t r = gfind<TH>(b.G, lat, d, ldcg(b.G + d), b.err, b.walk_cap ? b.walk_cap : kFindCap);
-              roots[gi + k] = (LabelT)gsite(lat, r);
-            }
+        for (int k = 0; k < 4; ++k)
+          rv[k] = (c[k] & kClosed) ? (LabelT)global_index(lat, x0, y0, c[k] & kIdx) : oroot[c[k]];
+        if (lat.vec4 && lx0 + 4 <= w) {
+          // four roots at once (gi is a multiple of 4 when L is)
+          if constexpr (sizeof(LabelT) == 4) {
+            *reinterpret_cast<uint4*>(roots + gi) = make_uint4((uint32_t)rv[0], (uint32_t)rv[1], (uint32_t)rv[2], (uint32_t)rv[3]);
+          } else {
+            *reinterpret_cast<ulonglong2*>(roots + gi) = make_ulonglong2(rv[0], rv[1]);
+            *reinterpret_cast<ulonglong2*>(roots + gi + 2) = make_ulonglong2(rv[2], rv[3]);
           }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (lx0 + k < w) roots[gi + k] = rv[k];
         }
       } else {
         uint32_t ok = 0;  // old spins (XY only)

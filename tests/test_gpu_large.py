@@ -156,3 +156,43 @@ def test_production_size_from_host_with_banded_upload_matches_the_oracle():
     assert [int(x) for x in E] == g["E"]
     assert [[int(v) for v in row] for row in n] == g["n"]
     assert hashlib.sha256(np.ascontiguousarray(spins).tobytes()).hexdigest() == g["spins_sha256"]
+
+
+def _node_word_fits(L, tile_h):
+    """Whether the global union-find's words carry node indices at this size
+    (key bits 2*xb plus node-index bits within 64), as the library decides."""
+    xb = max(1, (L - 1).bit_length())
+    nodes = -(-L // 128) * -(-L // tile_h) * (2 * tile_h + 256)
+    return 2 * xb + max(1, (nodes - 1).bit_length()) <= 64
+
+
+def test_largest_lattice_both_node_word_forms_agree():
+    """L = 131072 (1.7e10 sites, beyond 2^32): with 128-row tiles the global
+    union-find's words carry the parent's node index, with 16-row tiles
+    (2.4e9 nodes) they carry its open slot and the node is computed from the
+    site key.  Two sweeps from the same random start must give the same
+    spins and observables, and the observables must match a recount."""
+    import torch
+    Lb, q, seed, n = 131072, 2, 17, 2
+    assert _node_word_fits(Lb, 128) and not _node_word_fits(Lb, 16)
+    out = []
+    ref = None
+    for th in (128, 16):
+        with sw.Sim(Lb, q, sw.tc(q), seed, tile_h=th) as s:
+            s.sweep(n)
+            E, nn = s.series(0, n + 1)
+            sp = torch.empty(Lb * Lb, dtype=torch.uint8, device="cuda")
+            s.spins(out=sp)
+            torch.cuda.synchronize()
+        out.append((E, nn))
+        if ref is None:
+            ref = sp
+        else:
+            assert torch.equal(sp, ref)
+            del sp
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    # n[1] of the last configuration recounted from the spins
+    assert int((ref == 1).sum().item()) == int(out[0][1][-1][1])
+    assert int(out[0][1][-1].sum()) == Lb * Lb
+    del ref
+    torch.cuda.empty_cache()
