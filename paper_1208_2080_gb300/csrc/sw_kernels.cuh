@@ -1179,35 +1179,35 @@ __global__ void k_file(const __grid_constant__ Src src) {
 // ================================================================== k_resolve
 // Sec. 2 step (3) for open clusters: a thread per open root finds (and
 // compresses to) its global root and draws the cluster's new state, keyed
-// by the root's site index.  A tile's open slots are covered by
-// kResolvePer blocks (a thread per slot, the slots past the tile's count
-// leave at once), so every walk of the lattice is in flight together; the
-// tile's nodes are contiguous, so a warp's first loads share sectors.
+// by the root's site index.  A block of kResolveThreads per tile (a tile
+// has far fewer open roots than slots; a thread takes slots k, k + 256, ...
+// when it has more), so the walks of the whole lattice are in flight
+// together; the tile's nodes are contiguous, so a warp's first loads share
+// sectors.
 constexpr int kResolveThreads = 256;
-
-template <int TH>
-struct ResolveGrid {
-  static constexpr int kPer = (TileRec<TH>::kOpenCap + kResolveThreads - 1) / kResolveThreads;
-};
 
 template <int TH, typename LabelT, typename Src>
 __global__ void __launch_bounds__(kResolveThreads) k_resolve(const __grid_constant__ Src src) {
   using R = TileRec<TH>;
-  const uint32_t g = blockIdx.x / ResolveGrid<TH>::kPer;
-  const uint32_t k = (blockIdx.x % ResolveGrid<TH>::kPer) * kResolveThreads + threadIdx.x;
+  const uint32_t g = blockIdx.x;
   if (g >= src.ntiles()) return;
   const uint32_t rep = src.rep(g);
   const Bufs& b = src.bufs(rep);
   const uint32_t t = g - src.tile0(rep);
-  // the node's word is loaded with the tile's count (a slot past the count
-  // holds a stale word that is not used)
-  const uint64_t d = (uint64_t)t * R::kOpenCap + k;
-  const uint32_t n = b.ocnt[t];
-  const uint64_t w = ldcg(b.G + d);
-  if (k >= min(n, (uint32_t)R::kOpenCap)) return;
+  const uint64_t d0 = (uint64_t)t * R::kOpenCap;
+  // the first node's word is loaded with the tile's count (a slot past the
+  // count holds a stale word that is not used)
+  const uint32_t n0 = b.ocnt[t];
+  uint64_t w = ldcg(b.G + d0 + threadIdx.x);
+  const uint32_t n = min(n0, (uint32_t)R::kOpenCap);
   const Lattice& lat = src.lattice(rep);
-  const uint64_t r = gfind<TH>(b.G, lat, d, w, b.err, b.walk_cap ? b.walk_cap : kFindCap);
-  b.nso[d] = (uint8_t)pick_state(stream4_rk(b.rk, gsite(lat, r), (uint32_t)b.ctl[1], kDomSpin).x, b.q);
+  const uint32_t sweep = (uint32_t)b.ctl[1];
+  const uint32_t cap = b.walk_cap ? b.walk_cap : kFindCap;
+  for (uint32_t k = threadIdx.x; k < n; k += kResolveThreads) {
+    if (k != threadIdx.x) w = ldcg(b.G + d0 + k);
+    const uint64_t r = gfind<TH>(b.G, lat, d0 + k, w, b.err, cap);
+    b.nso[d0 + k] = (uint8_t)pick_state(stream4_rk(b.rk, gsite(lat, r), sweep, kDomSpin).x, b.q);
+  }
 }
 
 // ================================================================== k_recolor

@@ -124,9 +124,8 @@ cudaError_t launch_file_src(const Src& src, uint32_t nreps, cudaStream_t st) {
 
 template <int TH, typename LabelT, typename Src>
 cudaError_t launch_resolve_src(const Src& src, uint32_t ntiles, cudaStream_t st) {
-  const uint64_t blocks = (uint64_t)ntiles * ResolveGrid<TH>::kPer;
-  if (blocks == 0) return cudaSuccess;
-  k_resolve<TH, LabelT, Src><<<(unsigned)blocks, kResolveThreads, 0, st>>>(src);
+  if (ntiles == 0) return cudaSuccess;
+  k_resolve<TH, LabelT, Src><<<ntiles, kResolveThreads, 0, st>>>(src);
   return cudaGetLastError();
 }
 
