@@ -97,26 +97,56 @@ __global__ void k_wolff_seed(const __grid_constant__ WolffArgs a, int grow) {
 
 // Labelling mode, bonds of the step: a bond is active iff both ends are in
 // the seed's old state and its word is below the threshold.  A thread
-// writes the packed byte of 4 sites (bits 2k right, 2k+1 down).
+// writes the packed byte of 4 sites (bits 2k right, 2k+1 down).  When L is
+// a multiple of 4 the four spins, the four below them and the right
+// neighbour come in three loads, and the two sites of a pair share their
+// Philox call (one call gives the words of sites 2m and 2m+1).
 __global__ void __launch_bounds__(256) k_wolff_bonds(const __grid_constant__ WolffArgs a) {
   const uint32_t s_old = a.ctl->s_old;
   const uint32_t t = (uint32_t)a.ctl->step;
   const uint64_t L = a.L, groups = a.bp;
+  const bool vec = (L & 3u) == 0;
   for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L * groups;
        g += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t y = g / groups, x0 = (g - y * groups) * 4;
     const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
     uint32_t byte = 0;
-    for (int k = 0; k < 4 && x0 + k < L; ++k) {
-      const uint64_t x = x0 + k, i = y * L + x;
-      if (a.spin[i] != s_old) continue;
-      const uint64_t xr = (x + 1 == L) ? 0 : x + 1;
-      const bool er = a.spin[y * L + xr] == s_old, ed = a.spin[yd * L + x] == s_old;
-      if (!er && !ed) continue;
-      const Words4 w = stream4_rk(a.rk, i >> 1, t, kDomWolffBond);
-      const uint32_t wr = (i & 1u) ? w.z : w.x, wd = (i & 1u) ? w.w : w.y;
-      if (er && wr < a.thr) byte |= 1u << (2 * k);
-      if (ed && wd < a.thr) byte |= 2u << (2 * k);
+    if (vec) {
+      const uint64_t i0 = y * L + x0;  // a multiple of 4: the pairs are (i0, i0+1), (i0+2, i0+3)
+      const uint32_t sw = *reinterpret_cast<const uint32_t*>(a.spin + i0);
+      const uint32_t dw = *reinterpret_cast<const uint32_t*>(a.spin + yd * L + x0);
+      const uint32_t rn = a.spin[y * L + (x0 + 4 == L ? 0 : x0 + 4)];
+      const uint32_t rw = (sw >> 8) | (rn << 24);  // the right neighbours of the four sites
+      uint32_t need = 0;                          // per site: bit 0 right, bit 1 down candidate
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t sk = (sw >> (8 * k)) & 0xFFu;
+        if (sk != s_old) continue;
+        if (((rw >> (8 * k)) & 0xFFu) == s_old) need |= 1u << (2 * k);
+        if (((dw >> (8 * k)) & 0xFFu) == s_old) need |= 2u << (2 * k);
+      }
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const uint32_t np = (need >> (4 * p)) & 0xFu;
+        if (!np) continue;
+        const Words4 w = stream4_rk(a.rk, (i0 >> 1) + p, t, kDomWolffBond);
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};  // right, down of the even site; of the odd one
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (((np >> b) & 1u) && ws[b] < a.thr) byte |= 1u << (4 * p + b);
+      }
+    } else {
+      for (int k = 0; k < 4 && x0 + k < L; ++k) {
+        const uint64_t x = x0 + k, i = y * L + x;
+        if (a.spin[i] != s_old) continue;
+        const uint64_t xr = (x + 1 == L) ? 0 : x + 1;
+        const bool er = a.spin[y * L + xr] == s_old, ed = a.spin[yd * L + x] == s_old;
+        if (!er && !ed) continue;
+        const Words4 w = stream4_rk(a.rk, i >> 1, t, kDomWolffBond);
+        const uint32_t wr = (i & 1u) ? w.z : w.x, wd = (i & 1u) ? w.w : w.y;
+        if (er && wr < a.thr) byte |= 1u << (2 * k);
+        if (ed && wd < a.thr) byte |= 2u << (2 * k);
+      }
     }
     a.bonds[y * a.bp + x0 / 4] = (uint8_t)byte;
   }
@@ -128,11 +158,27 @@ __global__ void __launch_bounds__(256) k_wolff_flip(const __grid_constant__ Wolf
   const uint32_t r0 = a.roots[a.ctl->pad0];
   const uint32_t s_new = a.ctl->s_new;
   uint32_t n = 0;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    if (a.roots[i] == r0) {
-      a.spin[i] = (uint8_t)s_new;
-      ++n;
+  if ((a.N & 3u) == 0) {  // four roots per 16-byte load
+    const uint4* r4 = reinterpret_cast<const uint4*>(a.roots);
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.N / 4;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+      const uint4 r = __ldcs(r4 + v);
+      const uint32_t rv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (rv[k] == r0) {
+          a.spin[4 * v + k] = (uint8_t)s_new;
+          ++n;
+        }
+      }
+    }
+  } else {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+      if (a.roots[i] == r0) {
+        a.spin[i] = (uint8_t)s_new;
+        ++n;
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xFFFFFFFFu, n, o);
