@@ -960,31 +960,40 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
               }
             }
           }
-#pragma unroll
-          for (int k = 0; k < 8; ++k) cd[k] = (cd[k] & kMarkB) ? (cd[k] & kIdx16) : cd[k];
+          // final codes: a closed cluster's entry (kMarkA | payload, payload
+          // below 0x4000) is its code; an open root's (kMarkB | slot) becomes
+          // the slot -- both by clearing kMarkB, two codes per operation
+          constexpr uint32_t kKeep2 = ~(kMarkB | (kMarkB << 16));
+          const uint32_t cp[4] = {(cd[0] | (cd[1] << 16)) & kKeep2, (cd[2] | (cd[3] << 16)) & kKeep2,
+                                  (cd[4] | (cd[5] << 16)) & kKeep2, (cd[6] | (cd[7] << 16)) & kKeep2};
           const uint64_t gi = (y0 + yy) * L + x0 + cx;
           if ((L & 7u) == 0 && cx + 8 <= w) {
-            *reinterpret_cast<uint4*>(b.code + gi) = make_uint4(cd[0] | (cd[1] << 16), cd[2] | (cd[3] << 16),
-                                                                cd[4] | (cd[5] << 16), cd[6] | (cd[7] << 16));
+            *reinterpret_cast<uint4*>(b.code + gi) = make_uint4(cp[0], cp[1], cp[2], cp[3]);
           } else {
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-              if (cx + k < w) b.code[gi + k] = (uint16_t)cd[k];
+              if (cx + k < w) b.code[gi + k] = (uint16_t)(cp[k >> 1] >> (16 * (k & 1)));
           }
           // edge sites belong to open clusters: their codes are open slots
           if (yy == 0 || yy == h - 1) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
               if (cx + k < w) {
-                if (yy == h - 1) edge[2 * TH + cx + k] = (uint16_t)cd[k];
-                if (yy == 0) edge[2 * TH + kTW + cx + k] = (uint16_t)cd[k];
+                const uint16_t c = (uint16_t)(cp[k >> 1] >> (16 * (k & 1)));
+                if (yy == h - 1) edge[2 * TH + cx + k] = c;
+                if (yy == 0) edge[2 * TH + kTW + cx + k] = c;
               }
             }
           }
-          if (cx == 0) edge[TH + yy] = (uint16_t)cd[0];
+          if (cx == 0) edge[TH + yy] = (uint16_t)cp[0];
+          if (cx + 8 >= w) {  // the group that holds the row's last site
+            const int kl = w - 1 - cx;
+            uint32_t v = cp[0];
 #pragma unroll
-          for (int k = 0; k < 8; ++k)
-            if (cx + k == w - 1) edge[yy] = (uint16_t)cd[k];
+            for (int k = 1; k < 8; ++k)
+              if (k == kl) v = cp[k >> 1] >> (16 * (k & 1));
+            edge[yy] = (uint16_t)v;
+          }
         }
       }
       if (tid == 0) b.ocnt[t] = wcnt[0];
