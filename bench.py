@@ -49,8 +49,8 @@ LAUNCHES_PER_SWEEP = 4  # k_label_rows, k_merge, k_resolve, k_recolor
 # XY model (embedded clusters, M angles): the labeller reads the angle and
 # writes the code; the reflection reads code and angle and writes the
 # angle; the measurement reads the angle (halo rows come from L2).
-XY_PHASES = ["k_label_tile<XY>", "k_merge+k_resolve", "k_recolor<XY>", "k_xy_measure"]
-XY_ALG_BYTES_PER_SITE = {"k_label_tile<XY>": 3.0, "k_merge+k_resolve": 0.0, "k_recolor<XY>": 4.0,
+XY_PHASES = ["k_label_rows<XY>", "k_merge+k_resolve", "k_recolor<XY>", "k_xy_measure"]
+XY_ALG_BYTES_PER_SITE = {"k_label_rows<XY>": 3.0, "k_merge+k_resolve": 0.0, "k_recolor<XY>": 4.0,
                          "k_xy_measure": 1.0}
 THROTTLE = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 

@@ -379,7 +379,7 @@ typedef struct {
   uint32_t label_bits; /* 0 = auto (32 up to L = 32768, else 64), 32, 64 */
   double T;            /* temperature > 0 */
   uint64_t seed;       /* Philox key */
-  uint32_t tile_h;     /* 0 = auto (at most 64), 16, 32, 64 */
+  uint32_t tile_h;     /* 0 = auto (as sw_params), 16, 32, 64 or 128 */
   uint32_t ring;       /* configurations whose observables are kept (0 = 1024) */
   uint32_t init;       /* SW_INIT_RANDOM (angles from the init stream) or SW_INIT_ZERO */
   uint32_t measure;    /* 0: measure after every sweep; 2: only on request */

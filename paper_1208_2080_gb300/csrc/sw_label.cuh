@@ -239,7 +239,12 @@ __device__ __forceinline__ void stage_rows(const Src& src, uint32_t gg, uint8_t*
 // kRoots: closed clusters keep their local root in the code (no new state).
 // kFuse: the labeller also does the boundary unions (phase M; the fused
 // merge schedule).
-template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kFuse = false>
+// kXY: the XY model's embedded-cluster bonds (Sec. 5): a bond is a
+// candidate when both sites' projections on the sweep's axis have the same
+// (non-zero) sign, and active when its word is below the threshold of the
+// two sites' fold indices; clusters draw a coin (q = 2).
+template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kFuse = false,
+          bool kXY = false>
 __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
     k_label_rows(const __grid_constant__ Src src) {
   using C = RowCta<TH>;
@@ -363,6 +368,25 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
       else stage_rows<TH, kThreads>(src, g, sp, hal, false);
     }
     if (tid == 0) nsites += (uint32_t)(w * h);
+    if constexpr (kXY) {
+      // the projection class of every angle on this sweep's embedding axis
+      // (Wolff's embedding), built for the CTA's first tile (one lattice,
+      // one sweep): sign of sigma in bits 8-9 (1 negative, 2 positive, 0
+      // zero), fold index c of |sigma| = sin(pi c / M) below.  The shared
+      // observables area holds it (this form measures nothing).
+      if (g == blockIdx.x) {
+        const Bufs& xb = src.bufs(rep);
+        const uint32_t M = xb.M;
+        const uint32_t jx = pick_state(stream4_rk(xb.rk, 0ull, (uint32_t)xb.ctl[0], kDomAxis).x, M);
+        uint16_t* xcls = reinterpret_cast<uint16_t*>(sobs);
+        for (uint32_t k = tid; k < M; k += kThreads) {
+          const uint32_t a = (2 * k >= jx) ? 2 * k - jx : 2 * k + 2 * M - jx;  // (2k - j) mod 2M
+          const uint32_t sg = (a == 0 || a == M) ? 0u : (a < M ? 1u : 2u);
+          const uint32_t bm = a >= M ? a - M : a;
+          xcls[k] = (uint16_t)((sg << 8) | (bm < M - bm ? bm : M - bm));
+        }
+      }
+    }
     __syncthreads();  // staged spins visible; the previous tile is done with every shared array
     const Bufs& b = [&]() -> const Bufs& {
       if constexpr (Src::kMulti) return reinterpret_cast<const Rep*>(srec)[par].b;
@@ -392,7 +416,72 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
       vm[wi] = (ly < h) ? (nv >= 32 ? 0xFFFFFFFFu : (nv > 0 ? (1u << nv) - 1u : 0u)) : 0u;
       H[wi] = V[wi] = 0;
     }
-    if constexpr (kGiven) {
+    if constexpr (kXY) {
+      // four sites at a time: classes of the sites, their right and lower
+      // neighbours; one Philox call per two sites, as for the Potts bonds;
+      // thresholds from the lower triangle of the (fold index, fold index)
+      // table in global memory (read through L1)
+      const uint16_t* xcls = reinterpret_cast<const uint16_t*>(sobs);
+      auto thr_of = [&](uint32_t c, uint32_t d) -> uint32_t {
+        const uint32_t hi = c > d ? c : d, lo = c > d ? d : c;
+        return __ldg(b.tt + ((hi * (hi + 1)) >> 1) + lo);
+      };
+      const uint64_t rowg = (y0 + ly) * L + x0 + c0;
+#pragma unroll
+      for (int wi = 0; wi < kW; ++wi) {
+        if (vm[wi] == 0) continue;
+#pragma unroll 2
+        for (int gq = 0; gq < 8; ++gq) {
+          const uint32_t sh = 4 * gq;
+          const uint32_t m4 = (vm[wi] >> sh) & 0xFu;
+          if (!m4) continue;
+          const int cc = c0 + 32 * wi + 4 * gq;
+          const uint32_t sv = *reinterpret_cast<const uint32_t*>(sp + swz(ly, cc));
+          const uint32_t sn = cc + 4 < kTW ? *reinterpret_cast<const uint32_t*>(sp + swz(ly, cc + 4))
+                                            : *reinterpret_cast<const uint32_t*>(hal + 4 * ly);
+          const uint32_t sd = *reinterpret_cast<const uint32_t*>(sp + swz(ly + 1, cc));
+          uint32_t cs[5], cl[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            cs[k] = xcls[(sv >> (8 * k)) & 0xFFu];
+            cl[k] = xcls[(sd >> (8 * k)) & 0xFFu];
+          }
+          cs[4] = xcls[sn & 0xFFu];
+          uint32_t er = 0, ed = 0;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t sg = cs[k] >> 8;
+            er |= (sg != 0u && sg == (cs[k + 1] >> 8)) ? (1u << k) : 0u;
+            ed |= (sg != 0u && sg == (cl[k] >> 8)) ? (1u << k) : 0u;
+          }
+          er &= m4;
+          ed &= m4;
+          if (er | ed) {
+            const uint64_t i0 = rowg + 32 * wi + sh;
+            const uint64_t pa = i0 >> 1;
+            const Words4 A = philox(pa, kDomBond);
+            const Words4 B = philox(pa + 1, kDomBond);
+            uint32_t wr[4], wd[4];
+            if ((i0 & 1u) == 0u) {
+              wr[0] = A.x; wd[0] = A.y; wr[1] = A.z; wd[1] = A.w;
+              wr[2] = B.x; wd[2] = B.y; wr[3] = B.z; wd[3] = B.w;
+            } else {
+              const Words4 Cc = philox(pa + 2, kDomBond);
+              wr[0] = A.z; wd[0] = A.w; wr[1] = B.x; wd[1] = B.y;
+              wr[2] = B.z; wd[2] = B.w; wr[3] = Cc.x; wd[3] = Cc.y;
+            }
+            uint32_t br = 0, bd = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              if ((er >> k) & 1u) br |= (wr[k] < thr_of(cs[k] & 0xFFu, cs[k + 1] & 0xFFu) ? 1u : 0u) << k;
+              if ((ed >> k) & 1u) bd |= (wd[k] < thr_of(cs[k] & 0xFFu, cl[k] & 0xFFu) ? 1u : 0u) << k;
+            }
+            H[wi] |= br << sh;
+            V[wi] |= bd << sh;
+          }
+        }
+      }
+    } else if constexpr (kGiven) {
       if (ly < h) {
         const uint8_t* brow = b.bonds + (y0 + ly) * lat.bp;
 #pragma unroll

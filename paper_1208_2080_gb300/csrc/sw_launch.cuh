@@ -46,11 +46,15 @@ cudaError_t configure_on_device(Kern kern, int threads, int smem, int smem_max, 
   return cudaSuccess;
 }
 
-// Shared memory of the Potts labeller for a source: the per-state histogram
-// (q > 4, or any replica batch) needs the larger layout.
-template <int TH, bool kGiven, typename Src>
+// Shared memory of the labeller for a source: the per-state histogram
+// (q > 4, or any replica batch) and the XY form's class table need the
+// larger layout.
+template <int TH, bool kGiven, typename Src, bool kXY = false>
 int rows_smem(const Src& src) {
-  if constexpr (kGiven) {
+  if constexpr (kXY) {
+    (void)src;
+    return RowSmem<TH>::kBytes;
+  } else if constexpr (kGiven) {
     (void)src;
     return RowSmem<TH>::kBytesSmallQ;
   } else if constexpr (Src::kMulti) {
@@ -61,32 +65,19 @@ int rows_smem(const Src& src) {
   }
 }
 
-// Potts labeller (k_label_rows): attributes and resident CTAs on this device.
-template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kFuse>
+// The labeller (k_label_rows): attributes and resident CTAs on this device.
+template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kFuse, bool kXY>
 cudaError_t configure_rows(int smem, int* resident_out) {
   static std::atomic<int> resident[2][kMaxDevices];
   const int big = smem > RowSmem<TH>::kBytesSmallQ ? 1 : 0;
-  return configure_on_device(k_label_rows<TH, LabelT, kGiven, kRoots, Src, kFuse>, RowCta<TH>::kThreads, smem,
-                             RowSmem<TH>::kBytes, resident[big], resident_out);
-}
-
-// XY labeller (k_label_tile<XY>): attributes and resident CTAs on this device.
-template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY>
-cudaError_t configure_tile(int* resident_out) {
-  static std::atomic<int> resident[kMaxDevices];
-  const int smem = kXY ? LabelSmem<TH>::kXYBytes : LabelSmem<TH>::kBytes;
-  return configure_on_device(k_label_tile<TH, LabelT, kGiven, kRoots, Src, kXY>, TileCta<TH>::kThreads, smem,
-                             smem, resident, resident_out);
+  return configure_on_device(k_label_rows<TH, LabelT, kGiven, kRoots, Src, kFuse, kXY>, RowCta<TH>::kThreads,
+                             smem, RowSmem<TH>::kBytes, resident[big], resident_out);
 }
 
 template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY = false, bool kFuse = false>
 cudaError_t configure_label(const Src& src, int* resident_out) {
-  if constexpr (kXY) {
-    (void)src;
-    return configure_tile<TH, LabelT, kGiven, kRoots, Src, kXY>(resident_out);
-  } else {
-    return configure_rows<TH, LabelT, kGiven, kRoots, Src, kFuse>(rows_smem<TH, kGiven>(src), resident_out);
-  }
+  return configure_rows<TH, LabelT, kGiven, kRoots, Src, kFuse, kXY>(rows_smem<TH, kGiven, Src, kXY>(src),
+                                                                      resident_out);
 }
 
 // One labelling launch: a persistent grid of as many tile CTAs as fit.
@@ -97,13 +88,8 @@ cudaError_t launch_label_src(const Src& src, uint32_t ntiles, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const uint32_t grid = ntiles < (uint32_t)resident ? ntiles : (uint32_t)resident;
   if (grid == 0) return cudaSuccess;
-  if constexpr (kXY) {
-    k_label_tile<TH, LabelT, kGiven, kRoots, Src, kXY>
-        <<<grid, TileCta<TH>::kThreads, LabelSmem<TH>::kXYBytes, st>>>(src);
-  } else {
-    k_label_rows<TH, LabelT, kGiven, kRoots, Src, kFuse>
-        <<<grid, RowCta<TH>::kThreads, rows_smem<TH, kGiven>(src), st>>>(src);
-  }
+  k_label_rows<TH, LabelT, kGiven, kRoots, Src, kFuse, kXY>
+      <<<grid, RowCta<TH>::kThreads, rows_smem<TH, kGiven, Src, kXY>(src), st>>>(src);
   return cudaGetLastError();
 }
 
@@ -170,9 +156,7 @@ cudaError_t sweep_th(uint32_t th, const Src& src, uint32_t ntiles, cudaStream_t 
     case 16: return sweep_src<16, LabelT, Src, kXY>(src, ntiles, nreps, fused, st, ev);
     case 32: return sweep_src<32, LabelT, Src, kXY>(src, ntiles, nreps, fused, st, ev);
     case 64: return sweep_src<64, LabelT, Src, kXY>(src, ntiles, nreps, fused, st, ev);
-    case 128:
-      if constexpr (!kXY) return sweep_src<128, LabelT, Src, false>(src, ntiles, nreps, fused, st, ev);
-      else return cudaErrorInvalidValue;
+    case 128: return sweep_src<128, LabelT, Src, kXY>(src, ntiles, nreps, fused, st, ev);
     default: return cudaErrorInvalidValue;
   }
 }

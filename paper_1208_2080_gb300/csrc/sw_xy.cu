@@ -269,9 +269,8 @@ int sw_xy_create(const sw_xy_params* prm, sw_xy** out) {
   if (lb != 32 && lb != 64) return SW_ERR_INVAL;
   if (lb == 32 && L * L > (1ull << 32)) return SW_ERR_INVAL;
   // the XY form of the labeller takes tiles of at most 64 rows
-  uint32_t th = pick_tile_h(L, prm->tile_h);
-  if (!prm->tile_h && th > 64) th = 64;
-  if (th != 16 && th != 32 && th != 64) return SW_ERR_INVAL;
+  const uint32_t th = pick_tile_h(L, prm->tile_h);
+  if (th != 16 && th != 32 && th != 64 && th != 128) return SW_ERR_INVAL;
 
   sw_xy* s = new (std::nothrow) sw_xy();
   if (!s) return SW_ERR_NOMEM;

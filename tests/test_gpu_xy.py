@@ -32,7 +32,7 @@ def test_matches_oracle(L, M):
         _compare(L, M, T, 1000 * L + 10 * M + k, 6)
 
 
-@pytest.mark.parametrize("tile_h", [16, 32, 64])
+@pytest.mark.parametrize("tile_h", [16, 32, 64, 128])
 @pytest.mark.parametrize("bits", [32, 64])
 def test_tile_heights_and_label_widths(tile_h, bits):
     _compare(300, 256, sw.T_KT, 77, 5, tile_h=tile_h, label_bits=bits)
