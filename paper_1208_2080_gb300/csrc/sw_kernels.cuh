@@ -4,18 +4,15 @@
 // 128 x TH tiles (tile t = ty*ntx + tx, origin (128*tx, TH*ty); the last
 // tile row/column is ragged when TH or 128 does not divide L):
 //
-//   k_label_tile  (persistent; a CTA per tile at a time)  Sec. 2 steps
-//       (1)+(2), tile-local part: stage the tile's uint8 spins plus a
-//       one-site right/down halo in shared memory; draw the bonds (Philox,
-//       one call per two sites); measure E_sat / n[s] of the configuration
-//       it reads (Sec. 4); label the tile with a shared-memory union-find:
-//       horizontal runs inside a warp's 128-site row come from one
-//       __ballot_sync, vertical bonds are atomicMin unions (redundant ones
-//       between the same two runs skipped); a cluster that touches the tile
-//       edge is "open", the others are complete and get their new state
-//       here (Sec. 2 step (3)), drawn once per cluster from their root =
-//       smallest site index.  Per site it writes a 16-bit code: 0x8000|state
-//       for a closed cluster, the slot of its open root otherwise.  For the
+//   k_label_rows  (sw_label.cuh; persistent, a CTA per tile at a time)
+//       Sec. 2 steps (1)+(2), tile-local part: draw the bonds (Philox, one
+//       call per two sites), measure E_sat / n[s] of the configuration it
+//       reads (Sec. 4), label the tile with a shared-memory union-find over
+//       horizontal run starts; a cluster that touches the tile edge is
+//       "open", the others are complete and get their new state there
+//       (Sec. 2 step (3)), drawn once per cluster from their root = smallest
+//       site index.  Per site it writes a 16-bit code: 0x8000|state for a
+//       closed cluster, the slot of its open root otherwise.  For the
 //       boundary pass it writes the open slots of the four edge lines, the
 //       cross-edge bond bits, and initialises the open roots' nodes of the
 //       global union-find (below).
@@ -30,7 +27,7 @@
 //   k_recolor     every site writes its new uint8 spin from its code.
 //
 // The XY form (kXY; Sec. 5, Wolff's embedded clusters) is the same sweep
-// with the embedded bond rule in k_label_tile and reflections in
+// with the embedded bond rule in k_label_rows and reflections in
 // k_recolor; clusters draw a coin (the state draw with q = 2).
 //
 // Union always links the larger root under the smaller one, so the final
@@ -47,12 +44,10 @@
 
 namespace swgb {
 
-constexpr int kTW = 128;                  // tile width (32 lanes x 4 sites)
-constexpr int kThreads = 512;             // threads per tile CTA
+constexpr int kTW = 128;                  // tile width
+constexpr int kThreads = 512;             // threads of a k_recolor block (a tile)
 constexpr int kWarps = kThreads / 32;
-constexpr int kSpPitch = 144;             // smem spin row: 128 sites, halo; 16-byte rows
-constexpr uint32_t kOpen = 0x80000000u;   // smem root flag: cluster touches tile edge
-constexpr uint32_t kIdx = 0x7FFFu;        // local index bits
+constexpr uint32_t kIdx = 0x7FFFu;        // payload bits of a closed code
 constexpr uint16_t kClosed = 0x8000u;     // code flag: cluster complete in tile
 constexpr uint32_t kFindCap = 1u << 24;   // bound on any global union-find walk
 constexpr uint32_t kLocalCap = 1u << 16;  // bound on any shared-memory walk
@@ -71,36 +66,6 @@ struct TileRec {
   static constexpr int kRightWords = (TH + 31) / 32;       // cross-right bits
   static constexpr int kBitWords = kRightWords + kTW / 32; // + cross-down bits
   static constexpr int kOpenCap = 2 * TH + 2 * kTW;        // open roots <= edge sites
-};
-
-// Tile CTA shape: a warp owns 4 consecutive rows, so a 128 x TH tile is
-// labelled by TH/4 warps.
-template <int TH>
-struct TileCta {
-  static constexpr int kRpw = 4;                 // rows per warp
-  static constexpr int kWarps = TH / kRpw;       // warps per CTA
-  static constexpr int kThreads = 32 * kWarps;
-  static constexpr int kMinBlocks = 128 / TH;    // keeps the register budget at 64
-};
-
-// Shared-memory layout of k_label_tile.
-template <int TH>
-struct LabelSmem {
-  static constexpr int kNW = TileCta<TH>::kWarps;
-  static constexpr int kP = 0;                                     // u32 [kTW*TH] union-find
-  static constexpr int kSpBuf = align16((TH + 1) * kSpPitch);      // one staged tile of spins
-  static constexpr int kSp = kP + 4 * kTW * TH;                    // u8 [2][kSpBuf] double buffer
-  static constexpr int kRbn = kSp + 2 * kSpBuf;                    // u8 [TH*32] right-bond nibbles
-  static constexpr int kQ = align16(kRbn + TH * 32);               // u16 [kNW*kTW] task queues
-  static constexpr int kCb = align16(kQ + 2 * kNW * kTW);          // u32 cross bits
-  static constexpr int kCnt = align16(kCb + 4 * TileRec<TH>::kBitWords);  // u32 [kNW]
-  static constexpr int kObs = align16(kCnt + 4 * kNW);             // u32 [1 + 256]
-  static constexpr int kCl = align16(kObs + 4 * 257);              // u16 [kTW*TH] root lists
-  static constexpr int kBytes = align16(kCl + 2 * kTW * TH);
-  // XY form only: the bond thresholds of M <= 256 angles, lower triangle
-  // (129 * 130 / 2 entries), after the Potts layout
-  static constexpr int kXYTab = kBytes;
-  static constexpr int kXYBytes = align16(kXYTab + 4 * (129 * 130 / 2));
 };
 
 struct Lattice {
@@ -130,7 +95,7 @@ struct Bufs {
   uint64_t seed;
   uint32_t thr, q;
   uint32_t ring_cap;
-  uint32_t measure;           // 1: k_label_tile accumulates observables of its input
+  uint32_t measure;           // 1: the labeller accumulates observables of its input
   uint32_t rk[20];            // Philox round keys of `seed` (see set_round_keys)
   uint32_t walk_cap;          // bound on a global union-find walk (0: kFindCap)
   uint32_t fuse;              // 1: the labeller unites across tile edges (no k_merge)
@@ -232,113 +197,6 @@ __device__ __forceinline__ void tile_geom(const Lattice& lat, uint32_t t, int TH
   const uint64_t rw = lat.L - x0, rh = lat.L - y0;
   w = rw < (uint64_t)kTW ? (int)rw : kTW;
   h = rh < (uint64_t)TH ? (int)rh : TH;
-}
-
-// ---------------------------------------------------------------- shared-memory union-find
-// Entries are tile-local site indices and every parent is <= its child, so a
-// walk strictly decreases and ends at a root (bounded anyway).  Path halving
-// stores only replace a parent by one of its ancestors, which cannot undo a
-// concurrent atomicMin link (the union retries with the old parent).
-__device__ __forceinline__ uint32_t find_local(uint32_t* P, uint32_t x, uint32_t& bad) {
-  volatile uint32_t* vp = P;
-  for (uint32_t it = 0; it < kLocalCap; ++it) {
-    const uint32_t p = vp[x];
-    if (p == x) return x;
-    const uint32_t gp = vp[p];
-    if (gp == p) return p;
-    vp[x] = gp;
-    x = gp;
-  }
-  bad = 1;
-  return x;
-}
-
-// Read-only walk, for the compression pass: there, every run start must end
-// up pointing straight at its root, which halving stores by other threads
-// could undo.
-__device__ __forceinline__ uint32_t root_local(const uint32_t* P, uint32_t x, uint32_t& bad) {
-  const volatile uint32_t* vp = P;
-  for (uint32_t it = 0; it < kLocalCap; ++it) {
-    const uint32_t p = vp[x];
-    if (p == x) return x;
-    x = p;
-  }
-  bad = 1;
-  return x;
-}
-
-__device__ __forceinline__ void unite_local(uint32_t* P, uint32_t a, uint32_t b, uint32_t& bad) {
-  for (uint32_t it = 0; it < kLocalCap; ++it) {
-    a = find_local(P, a, bad);
-    b = find_local(P, b, bad);
-    if (a == b) return;
-    if (a < b) {
-      const uint32_t tmp = a;
-      a = b;
-      b = tmp;
-    }
-    const uint32_t old = atomicMin(&P[a], b);  // link the larger root under the smaller
-    if (old == a) return;
-    a = old;  // a was no longer a root: join its new parent instead
-  }
-  bad = 1;
-}
-
-// Root of x once all unions are done (roots may carry flag bits above
-// kIdx); returns the root and its raw entry.  Halving stores touch only
-// non-root entries, which carry no flags.
-__device__ __forceinline__ uint32_t walk_root(uint32_t* P, uint32_t x, uint32_t& vroot, uint32_t& bad) {
-  volatile uint32_t* vp = P;
-  for (uint32_t it = 0; it < kLocalCap; ++it) {
-    const uint32_t v = vp[x];
-    const uint32_t p = v & kIdx;
-    if (p == x) {
-      vroot = v;
-      return x;
-    }
-    const uint32_t v2 = vp[p];
-    const uint32_t gp = v2 & kIdx;
-    if (gp == p) {
-      vroot = v2;
-      return p;
-    }
-    vp[x] = gp;
-    x = gp;
-  }
-  bad = 1;
-  vroot = 0;
-  return x;
-}
-
-// Read-only walk to the root, ignoring flag bits above kIdx (used while
-// other threads compress starts and flag roots).
-__device__ __forceinline__ uint32_t root_masked(const uint32_t* P, uint32_t x, uint32_t& bad) {
-  const volatile uint32_t* vp = P;
-  for (uint32_t it = 0; it < kLocalCap; ++it) {
-    const uint32_t p = vp[x] & kIdx;
-    if (p == x) return x;
-    x = p;
-  }
-  bad = 1;
-  return x;
-}
-
-// Warp-level compaction: lane l contributes the sites (4l+k, k in `mask`)
-// of row base `rowbase`; returns the number of tasks written to q[0..n).
-// The tasks are ordered by site k first, then by lane: one ballot per k
-// gives every position without a prefix scan.
-__device__ __forceinline__ uint32_t warp_enqueue(uint16_t* q, uint32_t mask, uint32_t rowbase,
-                                                 int lane) {
-  const uint32_t lt = (1u << lane) - 1u;
-  uint32_t total = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const uint32_t bk = __ballot_sync(0xFFFFFFFFu, (mask >> k) & 1u);
-    if ((mask >> k) & 1u) q[total + __popc(bk & lt)] = (uint16_t)(rowbase + 4 * lane + k);
-    total += __popc(bk);
-  }
-  __syncwarp();
-  return total;
 }
 
 // ---------------------------------------------------------------- global union-find
@@ -485,602 +343,6 @@ __device__ __forceinline__ uint32_t byte_mask(uint32_t nib) {
   // 4-bit site mask -> 0xFF per selected byte
   return ((nib & 1u) ? 0x000000FFu : 0u) | ((nib & 2u) ? 0x0000FF00u : 0u) |
          ((nib & 4u) ? 0x00FF0000u : 0u) | ((nib & 8u) ? 0xFF000000u : 0u);
-}
-
-// ================================================================== k_label_tile
-// Persistent: CTA c labels tiles c, c + gridDim.x, ...; while it works on one
-// tile the next tile's spin rows are already in flight into the second
-// shared staging buffer (cp.async).
-//
-// kGiven: bonds are read from b.bonds instead of drawn (labelling-only entry).
-// kRoots: closed clusters keep their local root in the code (no new state).
-//
-// Union-find entries P[j] hold tile-local site indices j = ly*128 + lx
-// (15 bits).  A site that is not the start of its horizontal run keeps
-// pointing at its run start for the whole tile; only run starts take part
-// in unions, so only they are compressed, and every site's root is
-// P[P[j] & kIdx] & kIdx.  An open cluster's root carries kOpen until the
-// root lists are built; then every root entry's high half is the 16-bit
-// site code of its cluster (0x8000|state closed, the open-root slot open;
-// the labelling-only form keeps kOpen on open roots and no state).  Lane l
-// owns sites 4l..4l+3 of a row; its four entries are
-// moved with one 16-byte shared-memory access (conflict free); unions and
-// compressions are compacted into per-warp task queues so that all lanes
-// stay busy.
-template <int TH, typename LabelT, bool kGiven, bool kRoots, typename Src, bool kXY = false>
-__global__ void __launch_bounds__(TileCta<TH>::kThreads, TileCta<TH>::kMinBlocks)
-    k_label_tile(const __grid_constant__ Src src) {
-  static_assert(TH % 16 == 0 && kTW * TH <= 32768, "tile shape");
-  using S = LabelSmem<TH>;
-  using R = TileRec<TH>;
-  constexpr int kRpw = TileCta<TH>::kRpw;       // rows per warp
-  constexpr int kWarps = TileCta<TH>::kWarps;    // shadows the recolour CTA shape
-  constexpr int kThreads = TileCta<TH>::kThreads;
-  constexpr unsigned kFull = 0xFFFFFFFFu;
-
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* P = reinterpret_cast<uint32_t*>(smem + S::kP);
-  uint8_t* sp = smem + S::kSp;
-  uint8_t* rbn = smem + S::kRbn;
-  uint16_t* wq = reinterpret_cast<uint16_t*>(smem + S::kQ);
-  uint32_t* cbits = reinterpret_cast<uint32_t*>(smem + S::kCb);
-  uint32_t* wcnt = reinterpret_cast<uint32_t*>(smem + S::kCnt);
-  uint32_t* sobs = reinterpret_cast<uint32_t*>(smem + S::kObs);
-  uint16_t* clist = reinterpret_cast<uint16_t*>(smem + S::kCl);
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int lx0 = 4 * lane;
-  uint16_t* q = wq + warp * kTW;
-  const uint32_t total = src.ntiles();
-  uint32_t bad = 0, spin_max = 0;  // spin_max: byte-wise maximum of the spins read (BandSrc)
-
-  for (int k = tid; k < 257; k += kThreads) sobs[k] = 0;
-  uint32_t* xtt = reinterpret_cast<uint32_t*>(smem + S::kXYTab);  // XY form only
-  if constexpr (kXY) {
-    static_assert(!Src::kMulti, "the XY form labels one lattice");
-    const Bufs& b0 = src.bufs(0);
-    const uint32_t H1 = (b0.M >> 1) + 1;
-    for (uint32_t k = tid; k < H1 * (H1 + 1) / 2; k += kThreads) xtt[k] = __ldg(b0.tt + k);
-  }
-  uint32_t e_loc = 0, nsites = 0;
-  uint32_t ncnt[3] = {0, 0, 0};
-
-  // Observables accumulated so far (E_sat, and for q <= 4 the bit-plane
-  // counts c1 = n1 + n3, c2 = n2 + n3, c3 = n3 in registers, else n[s] in
-  // shared memory) go to the lattice's accumulator; n[0] follows from the
-  // site count.  Called by all threads.
-  auto flush = [&](const Bufs& fb, uint32_t fq) {
-    const bool fregs = fq <= 4;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e_loc += __shfl_xor_sync(kFull, e_loc, o);
-    if (lane == 0) atomicAdd(&sobs[0], e_loc);
-    if (fregs) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ncnt[k] += __shfl_xor_sync(kFull, ncnt[k], o);
-      if (lane == 0) {
-        atomicAdd(&sobs[2], ncnt[0] - ncnt[2]);                // n1
-        if (fq > 2) atomicAdd(&sobs[3], ncnt[1] - ncnt[2]);    // n2
-        if (fq > 3) atomicAdd(&sobs[4], ncnt[2]);              // n3
-      }
-    }
-    __syncthreads();
-    if (fregs && tid == 0) {
-      uint32_t rest = nsites;
-      for (uint32_t st = 1; st < fq; ++st) rest -= sobs[1 + st];
-      sobs[1] = rest;  // n0
-    }
-    __syncthreads();
-    for (uint32_t k = tid; k <= fq; k += kThreads)
-      if (sobs[k]) atomicAdd(&fb.acc[k], (unsigned long long)sobs[k]);
-    __syncthreads();
-    for (uint32_t k = tid; k <= fq; k += kThreads) sobs[k] = 0;
-    e_loc = 0;
-    nsites = 0;
-    ncnt[0] = ncnt[1] = ncnt[2] = 0;
-  };
-
-  // ---- stage a tile's spin rows (0..h-1 and the halo row h) plus each
-  // row's halo byte at column w into a shared buffer.  Rows start 4-byte
-  // aligned when L % 4 == 0: then the copies are asynchronous (cp.async)
-  // and the next tile is staged while this one is labelled; 16 bytes per
-  // copy (8 lanes a row, 4 rows a warp) when L % 16 == 0.
-  auto stage = [&](uint32_t gg, uint8_t* buf, bool async) {
-    const uint32_t fr = src.rep(gg);
-    const Lattice& fl = src.lattice(fr);
-    const uint8_t* fspin = src.bufs(fr).spin;
-    const uint64_t FL = fl.L;
-    uint64_t fx0, fy0;
-    int fw, fh;
-    tile_geom(fl, gg - src.tile0(fr), TH, fx0, fy0, fw, fh);
-    // halo row and column wrap around the lattice (x0 + w <= L, y0 + h <= L)
-    const uint64_t hx = (fx0 + fw == FL) ? 0 : fx0 + fw;
-    const uint64_t hy = (fy0 + fh == FL) ? 0 : fy0 + fh;
-    if (async && (FL & 15u) == 0 && (reinterpret_cast<uintptr_t>(fspin) & 15u) == 0) {
-      // w is a multiple of 16 here (x0 a multiple of 128, L of 16)
-      const int c16 = (lane & 7) * 16;
-      for (int ly = warp * 4 + (lane >> 3); ly <= fh; ly += 4 * kWarps) {
-        const uint64_t gy = (ly < fh) ? (fy0 + ly) : hy;
-        if (c16 < fw) cp_async16(buf + ly * kSpPitch + c16, fspin + gy * FL + fx0 + c16);
-      }
-      // halo column: 4 aligned bytes starting at column (x0 + w) mod L
-      for (int ly = tid; ly <= fh; ly += kThreads) {
-        const uint64_t gy = (ly < fh) ? (fy0 + ly) : hy;
-        cp_async4(buf + ly * kSpPitch + fw, fspin + gy * FL + hx);
-      }
-      return;
-    }
-    for (int ly = warp; ly <= fh; ly += kWarps) {
-      const uint64_t gy = (ly < fh) ? (fy0 + ly) : hy;
-      const uint8_t* row = fspin + gy * FL;
-      uint8_t* dst = buf + ly * kSpPitch;
-      if (async) {
-        if (lx0 < fw) cp_async4(dst + lx0, row + fx0 + lx0);
-        // halo column: 4 aligned bytes starting at column (x0 + w) mod L
-        if (lane == 31) cp_async4(dst + fw, row + hx);
-      } else {
-        uint32_t v = 0;
-        if (lx0 < fw) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (lx0 + k < fw) v |= (uint32_t)row[fx0 + lx0 + k] << (8 * k);
-        }
-        *reinterpret_cast<uint32_t*>(dst + lx0) = v;
-        __syncwarp();
-        if (lane == 0) dst[fw] = row[hx];
-      }
-    }
-  };
-  bool pre = false;  // this tile's spins were staged asynchronously
-  if (!kGiven && blockIdx.x < total && src.lattice(src.rep(blockIdx.x)).vec4) {
-    stage(blockIdx.x, sp, true);
-    cp_async_commit();
-    pre = true;
-  }
-
-  uint32_t it = 0;
-  for (uint32_t g = blockIdx.x; g < total; g += gridDim.x, ++it) {
-    const uint32_t rep = src.rep(g);
-    const Bufs& b = src.bufs(rep);
-    const Lattice& lat = src.lattice(rep);
-    const uint32_t t = g - src.tile0(rep);
-    const uint64_t L = lat.L;
-    const uint32_t q_states = b.q;
-    const bool measure = !kGiven && !kXY && b.measure;
-    const uint32_t sweep = kGiven ? 0u : (uint32_t)b.ctl[0];
-    const uint32_t qs = q_states <= 4 ? q_states - 1 : 0;  // states counted in registers
-    uint64_t x0, y0;
-    int w, h;
-    tile_geom(lat, t, TH, x0, y0, w, h);
-    uint8_t* spc = sp + (it & 1u) * S::kSpBuf;  // this tile's staged spins
-    if (tid < R::kBitWords) cbits[tid] = 0;
-    bool synced = false;  // a barrier already separates this tile from the last one
-    if (!kGiven) {
-      if (pre) {
-        cp_async_wait();
-        __syncthreads();  // every thread's copies of this tile have landed
-        synced = true;
-      } else {
-        stage(g, spc, false);
-      }
-      pre = false;
-      const uint32_t gn = g + gridDim.x;
-      if (gn < total && src.lattice(src.rep(gn)).vec4) {
-        stage(gn, sp + ((it + 1) & 1u) * S::kSpBuf, true);
-        cp_async_commit();
-        pre = true;
-      }
-    }
-    if constexpr (kXY) {
-      // projection class of every angle on this sweep's embedding axis
-      // (Wolff's embedding): sign of sigma in bits 8-9 (1 negative,
-      // 2 positive, 0 zero), fold index c of |sigma| = sin(pi c / M) below;
-      // built for the CTA's first tile only (one lattice, one sweep)
-      uint16_t* xcls = reinterpret_cast<uint16_t*>(sobs);
-      const uint32_t M = b.M;
-      const uint32_t jx = it == 0 ? pick_state(stream4_rk(b.rk, 0ull, sweep, kDomAxis).x, M) : 0u;
-      for (uint32_t k = tid; it == 0 && k < M; k += kThreads) {
-        const uint32_t a = (2 * k >= jx) ? 2 * k - jx : 2 * k + 2 * M - jx;  // (2k - j) mod 2M
-        const uint32_t sg = (a == 0 || a == M) ? 0u : (a < M ? 1u : 2u);
-        const uint32_t bm = a >= M ? a - M : a;
-        xcls[k] = (uint16_t)((sg << 8) | (bm < M - bm ? bm : M - bm));
-      }
-    }
-    if (tid == 0) nsites += (uint32_t)(w * h);
-    // synchronous staging, the zeroed cross bits (labelling from given
-    // bonds) or the XY class table must be visible before the bonds pass
-    if (!synced || (kXY && it == 0)) __syncthreads();
-
-    // ---- bonds, measurement, horizontal runs
-    uint32_t rowbits[kRpw];  // bits 0-3 internal right, 4-7 internal down, 8-11 run starts
-#pragma unroll
-    for (int rr = 0; rr < kRpw; ++rr) {
-      const int ly = warp * kRpw + rr;  // a warp owns a block of kRpw consecutive rows
-      uint32_t vm = 0;  // valid sites of this lane's group
-      if (ly < h) {
-        const int nv = w - lx0;
-        vm = nv >= 4 ? 0xFu : (nv > 0 ? (1u << nv) - 1u : 0u);
-      }
-      uint32_t br = 0, bd = 0;  // active bonds (right / down), all of them
-      if (kGiven) {
-        if (vm) {
-          const uint32_t byte = b.bonds[(y0 + ly) * lat.bp + ((x0 + lx0) >> 2)];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            br |= ((byte >> (2 * k)) & 1u) << k;
-            bd |= ((byte >> (2 * k + 1)) & 1u) << k;
-          }
-          br &= vm;
-          bd &= vm;
-        }
-      } else {
-        const uint32_t s = *reinterpret_cast<const uint32_t*>(spc + ly * kSpPitch + lx0);
-        if constexpr (Src::kCheck) spin_max = __vmaxu4(spin_max, s & byte_mask(vm));
-        const uint32_t sn = *reinterpret_cast<const uint32_t*>(spc + ly * kSpPitch + lx0 + 4);
-        const uint32_t sd = *reinterpret_cast<const uint32_t*>(spc + (ly + 1) * kSpPitch + lx0);
-        const uint32_t sr = __funnelshift_r(s, sn, 8);
-        uint32_t eqr, eqd;  // bond candidates: equal states (Potts), equal signs of sigma (XY)
-        uint32_t tr[4], td[4];
-        if constexpr (kXY) {
-          const uint16_t* xcls = reinterpret_cast<const uint16_t*>(sobs);
-          // threshold of fold indices (c, d): lower-triangle entry of the larger
-          auto thr_of = [&](uint32_t c, uint32_t d) -> uint32_t {
-            const uint32_t hi = c > d ? c : d, lo = c > d ? d : c;
-            return xtt[((hi * (hi + 1)) >> 1) + lo];
-          };
-          uint32_t cs[5], cd[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            cs[k] = xcls[(s >> (8 * k)) & 0xFFu];
-            cd[k] = xcls[(sd >> (8 * k)) & 0xFFu];
-          }
-          cs[4] = xcls[sn & 0xFFu];
-          eqr = eqd = 0;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const uint32_t sg = cs[k] >> 8;
-            eqr |= (sg != 0u && sg == (cs[k + 1] >> 8)) ? (1u << k) : 0u;
-            eqd |= (sg != 0u && sg == (cd[k] >> 8)) ? (1u << k) : 0u;
-            tr[k] = thr_of(cs[k] & 0xFFu, cs[k + 1] & 0xFFu);
-            td[k] = thr_of(cs[k] & 0xFFu, cd[k] & 0xFFu);
-          }
-          eqr &= vm;
-          eqd &= vm;
-        } else {
-          eqr = zero_bytes4(s ^ sr) & vm;  // right neighbour has the same state
-          eqd = zero_bytes4(s ^ sd) & vm;  // lower neighbour has the same state
-        }
-        if (!kXY && measure) {
-          e_loc += __popc(eqr) + __popc(eqd);
-          if (qs) {
-            // bit planes of the valid sites (q <= 4): bit 0 marks states 1, 3,
-            // bit 1 states 2, 3, both state 3
-            const uint32_t m1 = (vm * 0x00204081u) & 0x01010101u;  // bit 0 of each valid byte
-            ncnt[0] += __popc(s & m1);
-            if (qs > 1) {
-              const uint32_t s1 = (s >> 1) & m1;
-              ncnt[1] += __popc(s1);
-              ncnt[2] += __popc(s & s1);
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-              if (vm & (1u << k)) atomicAdd(&sobs[1 + ((s >> (8 * k)) & 0xFFu)], 1u);
-          }
-        }
-        if ((eqr | eqd) != 0u) {
-          const uint64_t i0 = (y0 + ly) * L + x0 + lx0;
-          const uint64_t pa = i0 >> 1;
-          const Words4 A = stream4_rk(b.rk, pa, sweep, kDomBond);
-          const Words4 B = stream4_rk(b.rk, pa + 1, sweep, kDomBond);
-          uint32_t wr[4], wd[4];
-          if ((i0 & 1u) == 0u) {
-            wr[0] = A.x; wd[0] = A.y; wr[1] = A.z; wd[1] = A.w;
-            wr[2] = B.x; wd[2] = B.y; wr[3] = B.z; wd[3] = B.w;
-          } else {
-            const Words4 C = stream4_rk(b.rk, pa + 2, sweep, kDomBond);
-            wr[0] = A.z; wd[0] = A.w; wr[1] = B.x; wd[1] = B.y;
-            wr[2] = B.z; wd[2] = B.w; wr[3] = C.x; wd[3] = C.y;
-          }
-          uint32_t ur = 0, ud = 0;  // u < thr per site
-          if constexpr (kXY) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              ur |= (wr[k] < tr[k] ? 1u : 0u) << k;
-              ud |= (wd[k] < td[k] ? 1u : 0u) << k;
-            }
-          } else {
-            ur = lt_mask4(wr, b.thr);
-            ud = lt_mask4(wd, b.thr);
-          }
-          br = eqr & ur;
-          bd = eqd & ud;
-        }
-        if (b.bonds && vm) {
-          uint32_t byte = 0;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) byte |= (((br >> k) & 1u) << (2 * k)) | (((bd >> k) & 1u) << (2 * k + 1));
-          b.bonds[(y0 + ly) * lat.bp + ((x0 + lx0) >> 2)] = (uint8_t)byte;
-        }
-      }
-      // internal vs cross-edge bonds
-      const int last = w - 1 - lx0;  // position of the tile's last column in this group
-      const uint32_t rint = (last >= 4) ? 0xFu : (last > 0 ? (1u << last) - 1u : 0u);
-      if (last >= 0 && last < 4 && ((br >> last) & 1u)) atomicOr(&cbits[ly >> 5], 1u << (ly & 31));
-      if (ly == h - 1) {
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const uint32_t v = (lane >> 3) == m ? (bd & 0xFu) << (4 * (lane & 7)) : 0u;
-          const uint32_t word = __reduce_or_sync(kFull, v);
-          if (lane == 0) cbits[R::kRightWords + m] = word;
-        }
-      }
-      const uint32_t r4 = br & rint;
-      const uint32_t d4 = (ly < h - 1) ? bd : 0u;
-      // horizontal runs: a site whose left bond is inactive starts a run;
-      // every site's provisional label is its run start (one ballot per row)
-      uint32_t prev3 = __shfl_up_sync(kFull, (r4 >> 3) & 1u, 1);
-      if (lane == 0) prev3 = 0;
-      const uint32_t brk = (~((r4 << 1) | prev3)) & 0xFu;
-      rowbits[rr] = r4 | (d4 << 4) | ((brk & vm) << 8);
-      const uint32_t Bm = __ballot_sync(kFull, brk != 0u);
-      const int lb = brk ? 31 - __clz(brk) : 0;
-      const uint32_t below = Bm & ((1u << lane) - 1u);
-      const int src = below ? 31 - __clz(below) : 0;
-      const int lbs = __shfl_sync(kFull, lb, src);
-      const uint32_t rowbase = (uint32_t)(ly * kTW);
-      // run start of each site: itself if it breaks the run, else the start
-      // of the site to its left (the first site inherits from earlier lanes)
-      const uint32_t st0 = rowbase + ((brk & 1u) ? (uint32_t)lx0 : (uint32_t)(4 * src + lbs));
-      const uint32_t st1 = (brk & 2u) ? rowbase + lx0 + 1 : st0;
-      const uint32_t st2 = (brk & 4u) ? rowbase + lx0 + 2 : st1;
-      const uint32_t st3 = (brk & 8u) ? rowbase + lx0 + 3 : st2;
-      *reinterpret_cast<uint4*>(P + rowbase + lx0) = make_uint4(st0, st1, st2, st3);
-      rbn[ly * 32 + lane] = (uint8_t)r4;
-    }
-    __syncthreads();
-
-    // ---- vertical unions.  Each warp first links its own rows top-down,
-    // one row pair at a time, so a new run is hung directly under an
-    // existing root and trees stay shallow; then the kWarps-1 row pairs that
-    // straddle two warps' blocks are linked.  Unions that repeat the left
-    // neighbour's union of the same two runs are skipped, the rest are
-    // compacted into the warp's task queue so all lanes stay busy.
-    auto link_rows = [&](int ly, uint32_t r4, uint32_t d4, uint32_t rb, uint32_t pb) {
-      uint32_t pd = __shfl_up_sync(kFull, (d4 >> 3) & 1u, 1);
-      uint32_t pr = __shfl_up_sync(kFull, (r4 >> 3) & 1u, 1);
-      if (lane == 0) pd = pr = pb = 0;
-      const uint32_t skip = ((d4 << 1) | pd) & ((r4 << 1) | pr) & ((rb << 1) | pb);
-      const uint32_t n = warp_enqueue(q, d4 & ~skip & 0xFu, (uint32_t)(ly * kTW), lane);
-      for (uint32_t i = lane; i < n; i += 32) {
-        const uint32_t a = q[i];
-        unite_local(P, P[a], P[a + kTW], bad);
-      }
-      __syncwarp();
-    };
-#pragma unroll
-    for (int rr = 0; rr + 1 < kRpw; ++rr) {
-      const int ly = warp * kRpw + rr;
-      if (ly < h - 1) {  // warp-uniform
-        const uint32_t rb = rowbits[rr + 1] & 0xFu;
-        const uint32_t pb = __shfl_up_sync(kFull, (rb >> 3) & 1u, 1);
-        link_rows(ly, rowbits[rr] & 0xFu, (rowbits[rr] >> 4) & 0xFu, rb, pb);
-      }
-    }
-    // no barrier: the lock-free unions are order independent, so a warp may
-    // link across the block boundary while its neighbour still links inside
-    {
-      const int ly = warp * kRpw + kRpw - 1;
-      if (warp + 1 < kWarps && ly < h - 1) {  // warp-uniform
-        const uint32_t rb = rbn[(ly + 1) * 32 + lane];
-        const uint32_t pb = lane > 0 ? (rbn[(ly + 1) * 32 + lane - 1] >> 3) & 1u : 0u;
-        link_rows(ly, rowbits[kRpw - 1] & 0xFu, (rowbits[kRpw - 1] >> 4) & 0xFu, rb, pb);
-      }
-    }
-    __syncthreads();
-
-    if (tid == 0) wcnt[0] = 0;  // open-slot counter of this tile
-
-    // ---- compress the run starts of the warp's rows (only starts can be
-    // roots; all rows in one batch, listed in the root-list area, which is
-    // free until the root lists), and flag clusters that touch the tile
-    // edge as open (the edge sites are spread over all threads)
-    {
-      uint16_t* tq = clist + warp * (kRpw * kTW);
-      const uint32_t jbase = (uint32_t)(warp * kRpw * kTW + lx0);
-      uint32_t smask = 0;
-#pragma unroll
-      for (int rr = 0; rr < kRpw; ++rr)
-        if (warp * kRpw + rr < h) smask |= ((rowbits[rr] >> 8) & 0xFu) << (4 * rr);
-      const uint32_t mine = (uint32_t)__popc(smask);
-      uint32_t inc = mine;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, inc, o);
-        if (lane >= o) inc += y;
-      }
-      uint32_t pos = inc - mine;
-      while (smask) {
-        const int bb = __ffs(smask) - 1;
-        smask &= smask - 1u;
-        tq[pos++] = (uint16_t)(jbase + (bb >> 2) * kTW + (bb & 3));
-      }
-      const uint32_t n = __shfl_sync(kFull, inc, 31);
-      __syncwarp();
-      for (uint32_t i = lane; i < n; i += 32) {
-        const uint32_t j = tq[i];
-        const uint32_t r = root_masked(P, j, bad);
-        if (r != j) P[j] = r;
-      }
-      __syncwarp();
-    }
-    {
-      const int nedge = 2 * (w + h);
-      for (int e = tid; e < nedge; e += kThreads) {
-        int lx, ly;
-        if (e < h) { lx = w - 1; ly = e; }
-        else if (e < 2 * h) { lx = 0; ly = e - h; }
-        else if (e < 2 * h + w) { lx = e - 2 * h; ly = 0; }
-        else { lx = e - 2 * h - w; ly = h - 1; }
-        const uint32_t r = root_masked(P, (uint32_t)(ly * kTW + lx), bad);
-        atomicOr(&P[r], kOpen);
-      }
-    }
-    __syncthreads();
-
-    // ---- root lists, warp-local: a run start j is a root iff P[j] == j.
-    // Closed roots fill the warp's region from the front, open ones from the
-    // back.
-    constexpr int kRegion = kRpw * kTW;
-    uint16_t* wl = clist + warp * kRegion;
-    // a lane's roots over all its rows (bit 4*rr + k), one prefix over the
-    // warp for all rows, then the lane writes its closed and open roots
-    uint32_t cmask = 0, omask = 0;
-#pragma unroll
-    for (int rr = 0; rr < kRpw; ++rr) {
-      const int ly = warp * kRpw + rr;
-      const uint32_t stb = (rowbits[rr] >> 8) & 0xFu;
-      if (ly < h && stb) {
-        const uint32_t j0 = (uint32_t)(ly * kTW + lx0);
-        const uint4 v4 = *reinterpret_cast<const uint4*>(P + j0);
-        const uint32_t v[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint32_t isroot = ((stb >> k) & 1u) & ((v[k] & kIdx) == j0 + k ? 1u : 0u);
-          const uint32_t open = v[k] >> 31;  // kOpen
-          cmask |= (isroot & (open ^ 1u)) << (4 * rr + k);
-          omask |= (isroot & open) << (4 * rr + k);
-        }
-      }
-    }
-    uint32_t nclosed, nopen;  // warp-uniform
-    {
-      const uint32_t mine = (uint32_t)__popc(cmask) | ((uint32_t)__popc(omask) << 16);
-      uint32_t inc = mine;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, inc, o);
-        if (lane >= o) inc += y;
-      }
-      const uint32_t excl = inc - mine;
-      uint32_t cpos = excl & 0xFFFFu, opos = excl >> 16;
-      const uint32_t jbase = (uint32_t)(warp * kRpw * kTW + lx0);
-      while (cmask) {
-        const int bb = __ffs(cmask) - 1;
-        cmask &= cmask - 1u;
-        wl[cpos++] = (uint16_t)(jbase + (bb >> 2) * kTW + (bb & 3));
-      }
-      while (omask) {
-        const int bb = __ffs(omask) - 1;
-        omask &= omask - 1u;
-        wl[kRegion - 1 - (opos++)] = (uint16_t)(jbase + (bb >> 2) * kTW + (bb & 3));
-      }
-      const uint32_t total = __shfl_sync(kFull, inc, 31);
-      nclosed = total & 0xFFFFu;
-      nopen = total >> 16;
-    }
-    // ---- new state of each complete cluster, drawn once at its root, by the
-    // warp that listed it (its own rows: no other warp reads these entries
-    // before the next barrier, so this needs no barrier of its own)
-    __syncwarp();
-    if (!kRoots) {
-      for (uint32_t i = lane; i < nclosed; i += 32) {
-        const uint32_t j = wl[i];
-        const uint32_t stt =
-            pick_state(stream4_rk(b.rk, global_index(lat, x0, y0, j), sweep, kDomSpin).x, q_states);
-        P[j] = j | ((kClosed | stt) << 16);  // the high half is the site code
-      }
-    }
-    // ---- open roots get a block of slots in the tile's open list (in
-    // whatever order the warps arrive: a slot only names the root to later
-    // kernels, results do not depend on it) and their node of the global
-    // union-find, a root for now
-    {
-      uint32_t obase = 0;
-      if (lane == 0 && nopen) obase = atomicAdd(&wcnt[0], nopen);
-      obase = __shfl_sync(kFull, obase, 0);
-      for (uint32_t i = lane; i < nopen; i += 32) {
-        const uint32_t j = wl[kRegion - 1 - i];
-        const uint32_t slot = obase + i;
-        // the high half is the site code (the slot); the labelling-only form
-        // keeps the open flag to tell open from closed roots
-        P[j] = j | (kRoots ? kOpen : 0u) | (slot << 16);
-        const uint64_t d = (uint64_t)t * R::kOpenCap + slot;
-        b.G[d] = gword(lat, d, x0, y0, j, slot);
-      }
-    }
-    __syncthreads();
-    if (tid == 0) b.ocnt[t] = wcnt[0];
-
-    // ---- per-site codes and the edge lines
-    uint16_t* edge = b.edge + (uint64_t)t * R::kEdge;
-#pragma unroll
-    for (int rr = 0; rr < kRpw; ++rr) {
-      const int ly = warp * kRpw + rr;
-      if (ly < h && lx0 < w) {
-        const uint32_t rowbase = (uint32_t)(ly * kTW);
-        const uint4 v4 = *reinterpret_cast<const uint4*>(P + rowbase + lx0);
-        const uint32_t v[4] = {v4.x, v4.y, v4.z, v4.w};
-        uint32_t c[4];
-        // four independent two-step lookups (run start, root), no branches
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint32_t x = v[k] & kIdx;  // run start, or the root for a start
-          const uint32_t pr = P[x] & kIdx;
-          const uint32_t pvr = P[pr];
-          if constexpr (kRoots)
-            c[k] = (pvr & kOpen) ? ((pvr >> 16) & 0x1FFu) : (kClosed | pr);
-          else
-            c[k] = pvr >> 16;
-        }
-        const uint64_t gi = (y0 + ly) * L + x0 + lx0;
-        if (lat.vec4) {
-          *reinterpret_cast<uint2*>(b.code + gi) = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
-        } else {
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (lx0 + k < w) b.code[gi + k] = (uint16_t)c[k];
-        }
-        // edge sites belong to open clusters: their codes are open slots
-        const bool edge_row = (ly == 0 || ly == h - 1);
-        const int last = w - 1 - lx0;
-        if (edge_row || lane == 0 || (last >= 0 && last < 4)) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int lx = lx0 + k;
-            if (lx < w) {
-              if (lx == w - 1) edge[ly] = (uint16_t)c[k];
-              if (lx == 0) edge[TH + ly] = (uint16_t)c[k];
-              if (ly == h - 1) edge[2 * TH + lx] = (uint16_t)c[k];
-              if (ly == 0) edge[2 * TH + kTW + lx] = (uint16_t)c[k];
-            }
-          }
-        }
-      }
-    }
-    if (tid < R::kBitWords) b.ebits[(uint64_t)t * R::kBitWords + tid] = cbits[tid];
-    // no barrier here: the next tile touches shared memory that this tile
-    // still reads (P, root lists) only after its own first barrier, and the
-    // cross bits only through the threads that read them here
-    // a replica's observables go out when the CTA's next tile belongs to
-    // another replica (or there is none); until then they accumulate
-    if (Src::kMulti && measure) {
-      const uint32_t gn = g + gridDim.x;
-      if (gn >= total || src.rep(gn) != rep) flush(b, q_states);
-    }
-  }
-
-  // ---- observables of the configuration read (Sec. 4), once per CTA
-  if (!Src::kMulti && !kGiven && total > 0 && blockIdx.x < total) {
-    const Bufs& b0 = src.bufs(0);
-    if (b0.measure) flush(b0, b0.q);
-  }
-  if (bad) atomicOr(src.bufs(0).err, kErrLocal);
-  if constexpr (Src::kCheck) {
-    const uint32_t m2 = __vmaxu4(spin_max, spin_max >> 16);
-    if ((__vmaxu4(m2, m2 >> 8) & 0xFFu) >= src.bufs(0).q) atomicOr(src.bufs(0).err, kErrSpin);
-  }
 }
 
 // ================================================================== boundary unions

@@ -1,12 +1,11 @@
 // sw_label.cuh -- k_label_rows, the tile labeller of the Potts sweep with
 // one lane per half tile row.
 //
-// It computes what k_label_tile computes (Sec. 2 steps (1)-(3), tile-local
-// part, plus the measurement of Sec. 4) and writes the same records -- the
+// It labels a 128 x TH tile (Sec. 2 steps (1)-(3), tile-local part, plus the
+// measurement of Sec. 4) and writes the records of the boundary pass -- the
 // 16-bit site codes, the open slots of the four edge lines, the cross-edge
-// bond bits and the open roots' nodes of the global union-find -- so that
-// k_merge, k_resolve and k_recolor run unchanged after it.  What differs is
-// the work mapping:
+// bond bits and the open roots' nodes of the global union-find -- that
+// k_merge, k_resolve and k_recolor read.  Its work mapping:
 //
 //   * a lane owns 64 consecutive sites of one tile row (two 32-bit words),
 //     so a warp covers 16 rows of a 128-wide tile and a CTA of TH/16 warps
@@ -19,21 +18,26 @@
 //     bit at or below it: only run starts are union-find nodes, and no
 //     per-site parent is ever written;
 //   * the union-find entries are 16 bits (tile-local index j = ly*128 + lx),
-//     so a 128 x 64 tile needs 16 KB of shared memory; linking a root is a
+//     so a 128 x 128 tile needs 32 KB of shared memory; linking a root is a
 //     compare-and-swap of the 32-bit word that holds its entry.
 //
 // Phases of a tile (a barrier after each):
-//   A  bonds (Philox, one call per two sites), observables of the
-//      configuration read, cross-edge bond bits, run-start masks;
-//   B  vertical unions: each lane links its row to the row below over its
-//      64 columns, one union per vertical bond that does not repeat its
-//      left neighbour's pair of runs;
+//   A  bonds (Philox, one call per two sites; the XY form's embedded bond
+//      rule, or given bonds), observables of the configuration read,
+//      cross-edge bond bits, run-start masks;
+//   B  vertical unions: each warp first joins its 16 rows top-down with
+//      __syncwarp only (a forest whose band-top runs are local roots),
+//      pointer jumping joins the bands, and the remaining unions go through
+//      per-warp queues (lockstep walks, path splitting, CAS links);
 //   C  clusters that touch the tile edge are flagged open at their root;
-//   D  run starts are compressed to their root; a closed cluster draws its
-//      new state at its root (Sec. 2 step (3)), an open root takes a slot in
-//      the tile's open list and its node of the global union-find;
-//   F  per-site codes (16 sites' worth of lanes per row, coalesced 16-byte
-//      stores) and the edge lines.
+//      linked roots and the bands' parented starts are pointed at their
+//      roots (every start at most two links below its root);
+//   D  roots: a closed cluster draws its new state at its root (Sec. 2
+//      step (3)), an open root takes a slot in the tile's open list and its
+//      node of the global union-find;
+//   F  per-site codes (8-site groups, 16-byte stores) and the edge lines;
+//   M  (fused merge schedule only) the boundary unions of the edges this
+//      tile finished second on.
 //
 // Entry encoding in P: a plain index (< 0x4000) is a parent (a root names
 // itself); phase C adds 0x8000 to open roots; phase D replaces every root's
