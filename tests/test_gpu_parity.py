@@ -324,16 +324,19 @@ def test_set_spins_from_page_locked_host_memory(L):
             s.set_spins(pinned.numpy())
 
 
-@pytest.mark.parametrize("L,tile_h", [(5, 0), (64, 16), (130, 32), (1000, 64), (2048, 64)])
-def test_sweep_host_overlapped_upload_matches_oracle(L, tile_h):
+@pytest.mark.parametrize("L,tile_h,merge", [(5, 0, "kernel"), (64, 16, "kernel"), (130, 32, "fused"),
+                                          (1000, 64, "kernel"), (2048, 64, "kernel"), (2048, 128, "fused")])
+def test_sweep_host_overlapped_upload_matches_oracle(L, tile_h, merge):
     """sw_sweep_host: banded upload + labelling from a host configuration
-    (pageable and page-locked) gives the oracle's chain and observables."""
+    (pageable and page-locked) gives the oracle's chain and observables,
+    with either merge schedule (fused: the bands' labellers unite across
+    the tile edges themselves)."""
     import torch
     q, seed = 3, 40 + L
     T = sw.tc(q)
     s0 = oracle.init_spins(L, q, seed + 1)
     ref, E, n = oracle.run(L, q, T, seed, 3, spins=s0, sweep0=2)
-    with sw.Sim(L, q, T, seed, tile_h=tile_h) as s:
+    with sw.Sim(L, q, T, seed, tile_h=tile_h, merge=merge) as s:
         s.sweep(2)
         Eg, ng, cfg = s.sweep_host(s0, 3)
         assert cfg == 5
