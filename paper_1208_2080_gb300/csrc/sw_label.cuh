@@ -169,6 +169,24 @@ __device__ __forceinline__ void pack32(const uint8_t* sp, int y, int col, bool t
   p1 = c;
 }
 
+// The same 32 sites as bit planes 0, 1 and 2 (states below 8).
+__device__ __forceinline__ void pack32x3(const uint8_t* sp, int y, int col, uint32_t& p0, uint32_t& p1,
+                                         uint32_t& p2) {
+  const uint4 u = *reinterpret_cast<const uint4*>(sp + swz(y, col));
+  const uint4 v = *reinterpret_cast<const uint4*>(sp + swz(y, col + 16));
+  const uint32_t w[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+  uint32_t a = 0, c = 0, e = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    a |= plane4(w[k], 0) << (4 * k);
+    c |= plane4(w[k], 1) << (4 * k);
+    e |= plane4(w[k], 2) << (4 * k);
+  }
+  p0 = a;
+  p1 = c;
+  p2 = e;
+}
+
 // Even / odd bits of a 32-bit word, compacted into 16 bits (bond bytes:
 // bit 2k = right bond of site k, bit 2k+1 = down bond).
 __device__ __forceinline__ uint32_t even_bits(uint32_t x) {
@@ -273,6 +291,9 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
   // the replica table in global memory they would take registers.
   __shared__ __align__(16) unsigned char srec[Src::kMulti ? 2 * sizeof(Rep) : 16];
   __shared__ __align__(16) uint32_t srk[Src::kMulti ? 2 * 20 : 4];  // its Philox round keys, 16-byte aligned
+  // replica batch, 4 < q <= 8: the CTA's bit-plane subset counts of the
+  // current replica (|a0|, |a1|, |a2|, |a0 a1|, |a0 a2|, |a1 a2|, |a0 a1 a2|)
+  __shared__ uint32_t sc3[Src::kMulti ? 8 : 1];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int part = lane % kLpr;
@@ -284,6 +305,7 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
 
   for (int k = tid; k < (Src::kMulti ? 257 : (big_q ? 257 : 8)); k += kThreads) sobs[k] = 0;
   for (int k = tid; k < R::kBitWords; k += kThreads) cbits[k] = 0;
+  if (Src::kMulti && tid < 8) sc3[tid] = 0;
   uint32_t e_loc = 0, nsites = 0;
   uint32_t ncnt[3] = {0, 0, 0};
 
@@ -311,6 +333,21 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
       uint32_t rest = nsites;
       for (uint32_t st = 1; st < fq; ++st) rest -= sobs[1 + st];
       sobs[1] = rest;
+    }
+    if constexpr (Src::kMulti) {
+      // three bit planes (4 < q <= 8): n[s] = sum over the plane subsets T
+      // that contain the set bits of s of (-1)^|T - s| c_T, where c_T counts
+      // the sites with every plane of T set (the empty set: every site)
+      if (fq > 4 && fq <= 8 && tid == 0) {
+        const uint32_t cT[8] = {nsites, sc3[0], sc3[1], sc3[3], sc3[2], sc3[4], sc3[5], sc3[6]};
+        for (uint32_t st = 0; st < fq; ++st) {
+          uint32_t n = 0;
+          for (uint32_t T = st; T < 8; ++T)
+            if ((T & st) == st) n += (__popc(T ^ st) & 1u) ? 0u - cT[T] : cT[T];
+          sobs[1 + st] = n;
+        }
+        for (int k = 0; k < 7; ++k) sc3[k] = 0;
+      }
     }
     __syncthreads();
     for (uint32_t k = tid; k <= fq; k += kThreads)
@@ -505,17 +542,25 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
         }
       }
     } else {
-      const uint32_t np = q_states <= 2 ? 1u : (q_states <= 4 ? 2u : 0u);  // bit planes
+      // bit planes: one for q = 2, two for q <= 4; a replica batch also
+      // keeps q <= 8 in three planes (its state counts go to the shared
+      // histogram warp by warp), a lattice of its own takes the byte path
+      constexpr bool kP3 = Src::kMulti;
+      const uint32_t np = q_states <= 2 ? 1u : (q_states <= 4 ? 2u : ((kP3 && q_states <= 8) ? 3u : 0u));
       uint32_t eqr[kW], eqd[kW];
       if (np) {
-        const bool two = np == 2;
-        uint32_t a0[kW], a1[kW], d0[kW], d1[kW];
+        const bool two = np >= 2;
+        const bool three = kP3 && np == 3;
+        uint32_t a0[kW], a1[kW], a2[kW], d0[kW], d1[kW], d2[kW];
 #pragma unroll
-        for (int wi = 0; wi < kW; ++wi) a0[wi] = a1[wi] = 0;
+        for (int wi = 0; wi < kW; ++wi) a0[wi] = a1[wi] = a2[wi] = 0;
         uint32_t nb = 0;  // the byte right of this lane's range (last part: the halo column)
         if (ly <= h) {
 #pragma unroll
-          for (int wi = 0; wi < kW; ++wi) pack32(sp, ly, c0 + 32 * wi, two, a0[wi], a1[wi]);
+          for (int wi = 0; wi < kW; ++wi) {
+            if (three) pack32x3(sp, ly, c0 + 32 * wi, a0[wi], a1[wi], a2[wi]);
+            else pack32(sp, ly, c0 + 32 * wi, two, a0[wi], a1[wi]);
+          }
           if (part == kLpr - 1) nb = hal[4 * ly];  // column 128 (a narrower tile masks it)
           if constexpr (Src::kCheck) {
             if (ly < h) {
@@ -533,31 +578,68 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
         const uint32_t n0 = __shfl_down_sync(kFull, a0[0], 1), n1 = __shfl_down_sync(kFull, a1[0], 1);
         const uint32_t nr0 = part == kLpr - 1 ? (nb & 1u) : (n0 & 1u);
         const uint32_t nr1 = part == kLpr - 1 ? ((nb >> 1) & 1u) : (n1 & 1u);
+        uint32_t nr2 = 0;
+        if (three) {
+          const uint32_t n2 = __shfl_down_sync(kFull, a2[0], 1);
+          nr2 = part == kLpr - 1 ? ((nb >> 2) & 1u) : (n2 & 1u);
+        }
         // the row below: from the lane that owns it, or staged (last row of the warp)
 #pragma unroll
         for (int wi = 0; wi < kW; ++wi) {
           d0[wi] = __shfl_down_sync(kFull, a0[wi], kLpr);
           d1[wi] = __shfl_down_sync(kFull, a1[wi], kLpr);
+          d2[wi] = three ? __shfl_down_sync(kFull, a2[wi], kLpr) : 0u;
         }
         if (lane / kLpr == kRpw - 1 && ly < h) {
 #pragma unroll
-          for (int wi = 0; wi < kW; ++wi) pack32(sp, ly + 1, c0 + 32 * wi, two, d0[wi], d1[wi]);
+          for (int wi = 0; wi < kW; ++wi) {
+            if (three) pack32x3(sp, ly + 1, c0 + 32 * wi, d0[wi], d1[wi], d2[wi]);
+            else pack32(sp, ly + 1, c0 + 32 * wi, two, d0[wi], d1[wi]);
+          }
         }
+        // bit-plane subset counts of the three-plane form: |a0|, |a1|, |a2|,
+        // |a0 a1|, |a0 a2|, |a1 a2|, |a0 a1 a2|
+        uint32_t c3[7] = {0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
         for (int wi = 0; wi < kW; ++wi) {
           const uint32_t x0n = wi + 1 < kW ? (a0[wi + 1] & 1u) : nr0;
           const uint32_t x1n = wi + 1 < kW ? (a1[wi + 1] & 1u) : nr1;
           const uint32_t r0 = (a0[wi] >> 1) | (x0n << 31), r1 = (a1[wi] >> 1) | (x1n << 31);
-          eqr[wi] = ~((a0[wi] ^ r0) | (a1[wi] ^ r1)) & vm[wi];
-          eqd[wi] = ~((a0[wi] ^ d0[wi]) | (a1[wi] ^ d1[wi])) & vm[wi];
+          uint32_t dr = (a0[wi] ^ r0) | (a1[wi] ^ r1), dd = (a0[wi] ^ d0[wi]) | (a1[wi] ^ d1[wi]);
+          if (three) {
+            const uint32_t x2n = wi + 1 < kW ? (a2[wi + 1] & 1u) : nr2;
+            dr |= a2[wi] ^ ((a2[wi] >> 1) | (x2n << 31));
+            dd |= a2[wi] ^ d2[wi];
+          }
+          eqr[wi] = ~dr & vm[wi];
+          eqd[wi] = ~dd & vm[wi];
           if (measure) {
             e_loc += __popc(eqr[wi]) + __popc(eqd[wi]);
-            ncnt[0] += __popc(a0[wi] & vm[wi]);
-            if (two) {
-              ncnt[1] += __popc(a1[wi] & vm[wi]);
-              ncnt[2] += __popc(a0[wi] & a1[wi] & vm[wi]);
+            if (three) {
+              const uint32_t b0 = a0[wi] & vm[wi], b1 = a1[wi] & vm[wi], b2 = a2[wi] & vm[wi];
+              const uint32_t b01 = b0 & b1;
+              c3[0] += __reduce_add_sync(kFull, __popc(b0));
+              c3[1] += __reduce_add_sync(kFull, __popc(b1));
+              c3[2] += __reduce_add_sync(kFull, __popc(b2));
+              c3[3] += __reduce_add_sync(kFull, __popc(b01));
+              c3[4] += __reduce_add_sync(kFull, __popc(b0 & b2));
+              c3[5] += __reduce_add_sync(kFull, __popc(b1 & b2));
+              c3[6] += __reduce_add_sync(kFull, __popc(b01 & b2));
+            } else {
+              ncnt[0] += __popc(a0[wi] & vm[wi]);
+              if (two) {
+                ncnt[1] += __popc(a1[wi] & vm[wi]);
+                ncnt[2] += __popc(a0[wi] & a1[wi] & vm[wi]);
+              }
             }
           }
+        }
+        if (three && measure && lane == 0) {
+          // the warp's plane-subset counts into the CTA's; the flush turns
+          // them into state counts
+#pragma unroll
+          for (int k = 0; k < 7; ++k)
+            if (c3[k]) atomicAdd(&sc3[k], c3[k]);
         }
       } else {
         // q > 4: byte-wise comparisons, state counts in a shared histogram
@@ -589,11 +671,13 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
           }
         }
       }
-      // bond draws: one Philox call per two sites (right and down words)
+      // bond draws: one Philox call per two sites (right and down words);
+      // a replica batch reads the round keys from shared memory, so two
+      // groups in flight would not fit in the registers
       const uint64_t rowg = (y0 + ly) * L + x0 + c0;
 #pragma unroll
       for (int wi = 0; wi < kW; ++wi) {
-#pragma unroll 2
+#pragma unroll(Src::kMulti ? 1 : 2)
         for (int gq = 0; gq < 8; ++gq) {
           const uint32_t sh = 4 * gq;
           const uint32_t er = (eqr[wi] >> sh) & 0xFu, ed = (eqd[wi] >> sh) & 0xFu;

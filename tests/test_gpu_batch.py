@@ -38,6 +38,28 @@ def test_mixed_batch_matches_oracle(tile_h, graph, merge):
             assert np.array_equal(E, refE) and np.array_equal(nn, refn), r
 
 
+@pytest.mark.parametrize("tile_h,merge", [(128, "kernel"), (32, "fused")])
+def test_batch_three_plane_states_match_oracle(tile_h, merge):
+    """A replica batch keeps 4 < q <= 8 in three bit planes (state counts by
+    inclusion-exclusion over the plane subsets), q > 8 in bytes: spins and
+    every E_sat / n[s] equal the oracle's, for every such q, at ragged and
+    tile-spanning sizes, ordered, critical and disordered temperatures."""
+    L = [16, 37, 64, 130, 200, 256, 99, 144]
+    q = [5, 6, 7, 8, 9, 8, 5, 6]
+    T = [sw.tc(5), sw.tc(6), 0.5 * sw.tc(7), sw.tc(8), sw.tc(9), 0.3, 3.0, 1.05 * sw.tc(6)]
+    seed = [31, 32, 33, 34, 35, 36, 37, 38]
+    n = 7
+    with sw.Batch(L, q, T, seed, tile_h=tile_h, merge=merge) as b:
+        b.sweep(n)
+        for r in range(len(L)):
+            ref, refE, refn = oracle.run(L[r], q[r], T[r], seed[r], n)
+            assert np.array_equal(b.spins(r), ref), r
+            E, nn = b.series(r, 1, n)
+            assert np.array_equal(E, refE) and np.array_equal(nn, refn), r
+            E_now, n_now, _ = b.measure(r)
+            assert E_now == refE[-1] and np.array_equal(n_now[:q[r]], refn[-1]), r
+
+
 def test_batch_equals_single_lattices():
     p = synth.replica_batch(24, master_seed=99, k_min=6, k_max=9)
     n = 6
