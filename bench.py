@@ -544,6 +544,45 @@ def run_wolff(args, sw, torch):
                                 "note": "SW sweep updates every site each sweep"}}
 
 
+def single_equivalent(args, sw, torch, p, batch_ms):
+    """The batch's work at single-lattice speed: for each q of the mix and
+    T/T_c in {0.9, 1.0, 1.1}, one L=16384 lattice (16384 tiles of 128x128,
+    which fill the GPU about as the batch's 60,517 tiles do) from its random
+    start, timed
+    over the same sweeps as the batch (3 untimed, then batch_sweeps); a
+    replica's sites cost its q's time per site averaged over T by Simpson's
+    rule (T is uniform on [0.9, 1.1] T_c in the mix).  The batch against this
+    time is the cost of batching itself; the headline lattice (q = 2 at T_c)
+    is the cheapest case of the mix."""
+    import numpy as np
+    Ls = 16384
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per_site = {}
+    classes = {}
+    for q in sorted(set(int(x) for x in p["q"])):
+        tc = sw.tc(q)
+        t = []
+        for f in (0.9, 1.0, 1.1):
+            with sw.Sim(Ls, q, f * tc, 1000 + q) as s:
+                s.sweep(3)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                s.sweep(args.batch_sweeps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                s.sync()
+                t.append(e0.elapsed_time(e1) / args.batch_sweeps / (Ls * Ls))
+            torch.cuda.empty_cache()
+        per_site[q] = (t[0] + 4 * t[1] + t[2]) / 6
+        classes[q] = {"updates_per_ns_at_0.9_1.0_1.1_Tc": [1e-6 / x for x in t]}
+    sites = p["L"].astype(np.float64) ** 2
+    equiv_ms = float(sum(sites[r] * per_site[int(p["q"][r])] for r in range(len(sites))))
+    return {"L": Ls, "sweeps": args.batch_sweeps, "ms_per_batch_sweep": equiv_ms,
+            "spin_updates_per_ns": float(sites.sum()) / (equiv_ms * 1e6),
+            "batch_over_single": batch_ms / equiv_ms, "per_q": classes}
+
+
 def run_batched(args, sw, torch):
     """Replica sweeps/s of the 512-replica batch (L = 64..2048 log-uniform,
     q in {2,3,4,5,8}, T in [0.9, 1.1] T_c(q), one Philox key each): all
@@ -570,10 +609,19 @@ def run_batched(args, sw, torch):
         torch.cuda.synchronize()
         b.sync()
         ms = e0.elapsed_time(e1)
+        # where a batch sweep's time goes: the library's per-launch events
+        # over 10 further sweeps (launched directly, not through the graph)
+        b.profile(True)
+        b.sweep(10)
+        pms, pn = b.profile_read()
+        b.profile(False)
     out.update({"sweeps": args.batch_sweeps, "ms_per_batch_sweep": ms / args.batch_sweeps,
+                "phase_ms_per_sweep": {name: m / max(c, 1) for name, m, c in zip(PHASES, pms, pn)},
                 "replica_sweeps_per_s": R * args.batch_sweeps / (ms * 1e-3),
                 "spin_updates_per_ns": out["sites"] * args.batch_sweeps / (ms * 1e6)})
     torch.cuda.empty_cache()
+    if args.batch_equiv:
+        out["single_equiv"] = single_equivalent(args, sw, torch, p, ms / args.batch_sweeps)
     sims = [sw.Sim(int(p["L"][r]), int(p["q"][r]), float(p["T"][r]), int(p["seed"][r]))
             for r in range(R)]
     for s_ in sims:
@@ -614,6 +662,8 @@ def main():
     ap.add_argument("--batch-R", type=int, default=512, help="replicas in the batched measurement")
     ap.add_argument("--batch-sweeps", type=int, default=40, help="0 skips the batched measurement")
     ap.add_argument("--plain-sweeps", type=int, default=10)
+    ap.add_argument("--no-batch-equiv", dest="batch_equiv", action="store_false",
+                    help="skip the single-lattice equivalent of the batch")
     ap.add_argument("--wolff-steps", type=int, default=100, help="0 skips the Wolff measurement")
     ap.add_argument("--wolff-warmup", type=int, default=10)
     ap.add_argument("--wolff-L", type=int, default=16384)

@@ -4,11 +4,14 @@
     python -m paper_1208_2080_gb300.run potts --L 65536 --sweeps 3 --host
     python -m paper_1208_2080_gb300.run xy --L 16384 --M 256 --sweeps 5
     python -m paper_1208_2080_gb300.run wolff --L 4096 --q 2 --steps 10 --mode label
+    python -m paper_1208_2080_gb300.run batch --R 128 --sweeps 5 --tile-h 128
 
 Temperatures default to the critical point of each model (T_c of the
 q-state Potts model, T_KT of the XY model).  The start is all-zero; the time
-is CUDA events around all sweeps / steps.  Used as the small, fixed cases
-that profiles are taken on.
+is CUDA events around all sweeps / steps.  The batch is the replica mix of
+the batched workload (L = 64..2048 log-uniform, q in {2,3,4,5,8}, T in
+[0.9, 1.1] T_c(q); master seed 6), its first R replicas, from their seeded
+random starts.  Used as the small, fixed cases that profiles are taken on.
 """
 import argparse
 import json
@@ -16,7 +19,10 @@ import json
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("model", choices=["potts", "xy", "wolff"])
+    ap.add_argument("model", choices=["potts", "xy", "wolff", "batch"])
+    ap.add_argument("--R", type=int, default=128)
+    ap.add_argument("--tile-h", type=int, default=128)
+    ap.add_argument("--merge", default="kernel", choices=["kernel", "fused"])
     ap.add_argument("--L", type=int, default=4096)
     ap.add_argument("--q", type=int, default=2)
     ap.add_argument("--M", type=int, default=256)
@@ -52,6 +58,20 @@ def main():
             s.sync()
         out = {"E_sat": E, "n": [int(x) for x in n], "config": cfg}
         work = N * a.sweeps
+    elif a.model == "batch":
+        import synth
+        p = synth.replica_batch(512, master_seed=6)
+        R = a.R
+        T = None
+        with sw.Batch(p["L"][:R], p["q"][:R], p["T"][:R], p["seed"][:R], tile_h=a.tile_h, graph=False,
+                      merge=a.merge) as b:
+            e0.record(stream)
+            b.sweep(a.sweeps)
+            e1.record(stream)
+            E, n, cfg = b.measure(0)
+            b.sync()
+        out = {"E_sat_0": E, "config": cfg, "R": R}
+        work = float((p["L"][:R].astype("float64") ** 2).sum()) * a.sweeps
     elif a.model == "xy":
         T = sw.T_KT if a.T is None else a.T
         with sw.XY(a.L, a.M, T, a.seed, init="zero", label_bits=a.label_bits) as x:
