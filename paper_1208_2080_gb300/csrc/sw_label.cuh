@@ -71,6 +71,10 @@ struct RowCta {
   // a warp's work queue in the staging buffer: 512 entries (32 lanes x 16)
   static constexpr int kQCap = (TH + 1) * 128 / 4 / kWarps;
   static_assert(kQCap >= 512, "work queue");
+  // while L2 (a bitmap of the roots linked by unions, 4 words a row) is in
+  // use behind them, the queues hold kQ8 entries a lane
+  static constexpr int kQ8 = 12;
+  static_assert(kWarps * 32 * kQ8 + 4 * TH <= (TH + 1) * 128 / 4, "work queue beside L2");
 };
 
 // Shared memory of k_label_rows.
@@ -769,11 +773,11 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
 
     if (tid < R::kBitWords) b.ebits[(uint64_t)t * R::kBitWords + tid] = cbits[tid];
     // from here to phase F the staging buffer holds the warps' work queues
-    // (512 entries each, or 256 while L2 -- the roots linked by unions, a
-    // bitmap like NR -- is in use behind them)
+    // (512 entries each, or 32 * kQ8 while L2 -- the roots linked by unions,
+    // a bitmap like NR -- is in use behind them)
     uint32_t* Q = reinterpret_cast<uint32_t*>(sp) + warp * kQCap;
-    uint32_t* Q8 = reinterpret_cast<uint32_t*>(sp) + warp * 256;
-    uint32_t* L2 = reinterpret_cast<uint32_t*>(sp) + C::kWarps * 256;
+    uint32_t* Q8 = reinterpret_cast<uint32_t*>(sp) + warp * 32 * C::kQ8;
+    uint32_t* L2 = reinterpret_cast<uint32_t*>(sp) + C::kWarps * 32 * C::kQ8;
 
     // ================================================= B: vertical unions
     // Each lane looks at the vertical bonds from its row y to the row below
@@ -892,7 +896,7 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
       const uint32_t ja = (uint32_t)(ly * kTW), jc = ja + kTW;
       volatile uint32_t* vP32 = reinterpret_cast<volatile uint32_t*>(P);
       for (;;) {
-        const uint32_t nq = enqueue16<8>(rem, Q8, lane, [&](uint32_t x) {
+        const uint32_t nq = enqueue16<C::kQ8>(rem, Q8, lane, [&](uint32_t x) {
           return (ja + run_start64(Sa, x, (uint32_t)c0, Cw[0])) |
                  ((jc + run_start64(S1, x, (uint32_t)c0, c1)) << 16);
         });
@@ -983,7 +987,7 @@ __global__ void __launch_bounds__(RowCta<TH>::kThreads, RowCta<TH>::kMinBlocks)
       const uint32_t jb = (uint32_t)(ly * kTW + c0);
       __syncwarp();
       for (;;) {
-        const uint32_t nq = enqueue16<8>(rem, Q8, lane, [&](uint32_t x) { return jb + x; });
+        const uint32_t nq = enqueue16<C::kQ8>(rem, Q8, lane, [&](uint32_t x) { return jb + x; });
         if (nq == 0) break;  // warp-uniform
         uint32_t idx = (uint32_t)lane, sj = 0, x = 0;  // idle lanes look at entry 0
         bool act = false;
